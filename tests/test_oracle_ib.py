@@ -1,0 +1,185 @@
+"""Pins of the oracle's immersed-boundary stage (Sec. 2.2-2.4, Eqs. 12-27).
+
+* Support selection and interpolation/spreading are brute-forced against dense
+  operators built node by node over the whole lattice (Eqs. 14-15).
+* Spreading is the transpose of interpolation scaled by drs*ds (Eqs. 14-15).
+* Eq. 27's two sides agree when no support is clipped.
+* The thickness solve (Eqs. 22, 24-25) gives the flat-wall closed form
+  drs = 1 / sum(delta^2) and, on a circle, the constants of Sec. 4.4 within
+  ten percent (Fig. 4 is not printed as data).
+* Implicit direct forcing (Eq. 17) and implicit velocity correction (Eq. A50)
+  give the same force field (Appendix A).
+* BTDF reduces the boundary slip (Eq. 45) relative to DF (drs = dh), Sec. 5.2.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import oracle as O
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+
+
+def _dense_DI(s, X, Y, kind):
+    """Interpolation matrix by brute force over every node of the lattice."""
+    nx, ny = s.nx, s.ny
+    D = np.zeros((len(X), nx * ny))
+    for l in range(len(X)):
+        for y in range(ny):
+            for x in range(nx):
+                # periodic images so that wrapped supports are found too
+                w = 0.0
+                for ix in (-nx, 0, nx):
+                    for iy in (-ny, 0, ny):
+                        w += O.delta(kind, x + ix - X[l]) * O.delta(kind, y + iy - Y[l])
+                D[l, y * nx + x] = w
+    return D
+
+
+@pytest.mark.parametrize("kind", [2, 3, 4, 5])
+def test_support_and_operators_match_dense(kind):
+    nx, ny = 14, 12
+    s = O.Sim(nx, ny, 0.7, 0.0, 0, 0, 0.0, 0.0, kind, 1)
+    rng = np.random.default_rng(kind)
+    X = rng.uniform(0, nx, 7)
+    Y = rng.uniform(0, ny, 7)
+    X[0], Y[0] = 0.3, 11.8           # wraps across both periodic edges
+    X[1], Y[1] = 5.0, 6.5            # exact node / half-node offsets
+    b = s.add_body(X, Y, 0.9, drs=1.7)
+    D = _dense_DI(s, X, Y, kind)
+    for l in range(len(X)):
+        nodes, w = s.support(X[l], Y[l])
+        row = np.zeros(nx * ny)
+        np.add.at(row, nodes, w)
+        assert np.abs(row - D[l]).max() < 1e-15
+    fx = rng.standard_normal((ny, nx))
+    fy = rng.standard_normal((ny, nx))
+    Ux, Uy = s.interp(b, fx, fy)
+    assert np.abs(Ux - D @ fx.ravel()).max() < 1e-13
+    assert np.abs(Uy - D @ fy.ravel()).max() < 1e-13
+    Fx = rng.standard_normal(len(X))
+    Fy = rng.standard_normal(len(X))
+    gx, gy = s.spread(b, Fx, Fy)
+    assert np.abs(gx.ravel() - 1.7 * 0.9 * (D.T @ Fx)).max() < 1e-13
+    assert np.abs(gy.ravel() - 1.7 * 0.9 * (D.T @ Fy)).max() < 1e-13
+
+
+def test_support_clipped_by_walls():
+    s = O.Sim(10, 8, 0.7, 0.05, W.BCX_INOUT, W.BCY_FREESLIP, 0.0, 0.0, 4, 1)
+    nodes, w = s.support(0.4, 0.6)   # 4x4 support, 3 columns and 3 rows survive
+    assert len(nodes) == 9
+    assert (nodes >= 0).all() and (nodes < 80).all()
+
+
+@pytest.mark.parametrize("kind", [2, 3, 4])
+def test_eq27_both_sides_agree(kind):
+    s = O.Sim(40, 40, 0.7, 0.0, 0, 0, 0.0, 0.0, kind, 1)
+    b = W.circle_markers(20.2, 19.7, 12.0, 37)
+    bi = s.add_body(b.X, b.Y, b.ds)
+    rng = np.random.default_rng(0)
+    Fx, Fy = rng.standard_normal(37), rng.standard_normal(37)
+    fx, fy = s.spread(bi, Fx, Fy)
+    drs = s.body_drs(bi)
+    assert abs(fx.sum() - (Fx * b.ds * drs).sum()) < 1e-12
+    assert abs(fy.sum() - (Fy * b.ds * drs).sum()) < 1e-12
+
+
+@pytest.mark.parametrize("kind", [2, 3, 4, 5])
+@pytest.mark.parametrize("yoff", [0.0, 0.25, 0.5])
+def test_flat_wall_thickness_closed_form(kind, yoff):
+    """A periodic straight line of markers with ds = dh has A 1 = sum(delta^2) 1,
+    hence drs = 1 / sum_j delta(y_j - Y)^2 at every marker (Eqs. 22, 25)."""
+    nx, ny = 24, 12
+    s = O.Sim(nx, ny, 0.7, 0.0, W.BCX_PERIODIC, W.BCY_FREESLIP, 0.0, 0.0, kind, 1)
+    X = np.arange(nx) + 0.3
+    Y = np.full(nx, 5.0 + yoff)
+    b = s.add_body(X, Y, 1.0)
+    drs = s.drs_local(b)
+    ssq = sum(O.delta(kind, j - (5.0 + yoff)) ** 2 for j in range(ny))
+    if kind in (4, 5):
+        # These kernels split into equal even and odd halves, so the
+        # alternating vector is in the null space of A and the local solve is
+        # not unique; the uniform value of Eq. 26 still is.
+        assert abs(drs.mean() - 1.0 / ssq) < 1e-9
+        assert abs(drs.mean() - 8.0 / 3.0) < 1e-9
+    else:
+        assert np.abs(drs - 1.0 / ssq).max() < 1e-12
+    if kind == 3:
+        assert np.abs(drs - 2.0).max() < 1e-12
+
+
+@pytest.mark.parametrize("kind", [2, 3, 4])
+def test_circle_mean_thickness_near_paper(kind):
+    """Eq. 26 on a circle with ds ~ dh lands within 10% of the suggested
+    constants 1.4 / 1.9 / 2.6 (Sec. 4.4, Fig. 4)."""
+    vals = []
+    for d, n in ((20.0, 63), (40.0, 126)):
+        s = O.Sim(int(d) + 12, int(d) + 12, 0.7, 0.0, 0, 0, 0.0, 0.0, kind, 1)
+        b = W.circle_markers(d / 2 + 6, d / 2 + 6, d, n)
+        bi = s.add_body(b.X, b.Y, b.ds)
+        vals.append(s.drs_local(bi).mean())
+    paper = GOLD["drs_over_dh"][str(kind)]
+    for v in vals:
+        assert abs(v / paper - 1.0) < 0.10, (kind, vals)
+
+
+def test_idf_equals_ivc():
+    """Appendix A: f from Eq. 17 (any drs) equals f from Eqs. 32, 35 (drs = dh)."""
+    nx, ny = 16, 16
+    kind = 3
+    s = O.Sim(nx, ny, 0.7, 0.0, 0, 0, 0.0, 0.0, kind, 1)
+    b = W.circle_markers(8.1, 7.9, 7.0, 16)
+    drs = 1.9
+    bi = s.add_body(b.X, b.Y, b.ds, drs=drs)
+    n = len(b.X)
+    DI = np.zeros((n, nx * ny))
+    DE = np.zeros((nx * ny, n))
+    for l in range(n):
+        e = np.zeros(nx * ny)
+        e_l = np.zeros(n)
+        e_l[l] = 1.0
+        DE[:, l] = s.spread(bi, e_l, np.zeros(n))[0].ravel()
+    for k in range(nx * ny):
+        e = np.zeros(nx * ny)
+        e[k] = 1.0
+        DI[:, k] = s.interp(bi, e.reshape(ny, nx), np.zeros((ny, nx)))[0]
+    rng = np.random.default_rng(2)
+    ustar = 0.05 + 0.01 * rng.standard_normal(nx * ny)
+    rho = 1.0
+    rhs = 2 * rho * (0.0 - DI @ ustar)
+    f_idf = DE @ np.linalg.solve(DI @ DE, rhs)          # Eq. 17 then Eq. 13
+    DEI = DE / drs                                       # Eq. 28 (drs = dh)
+    A = DI @ DEI                                         # Eq. 22
+    du = np.linalg.solve(A, 0.0 - DI @ ustar)           # Eq. 32
+    f_ivc = 2 * rho * DEI @ du                           # Eq. 35
+    assert np.abs(f_idf - f_ivc).max() < 1e-12 * np.abs(f_idf).max()
+    # and IDF enforces no slip exactly at the markers (Eq. 16)
+    assert np.abs(DI @ (ustar + f_idf / (2 * rho))).max() < 1e-12
+
+
+def _slip(drs, steps=600, nf=1):
+    c = W.small_cylinder(delta=3)
+    c.drs = drs
+    c.nf = nf
+    s = O.Sim.from_case(c)
+    s.step(steps)
+    d = s.marker_diag(0)
+    return math.sqrt(np.mean(d["Ux"] ** 2 + d["Uy"] ** 2)) / c.u_in
+
+
+def test_btdf_slip_below_df_slip():
+    """Sec. 5.2 (Fig. 9): thickening the shell lowers the boundary error of Eq. 45."""
+    df = _slip(1.0)
+    btdf = _slip(O.drs_paper(3))
+    assert btdf < 0.5 * df, (btdf, df)
+
+
+def test_mdf_iterations_reduce_slip():
+    """Sec. 3.2: more forcing passes drive the marker velocity toward U_b."""
+    s1 = _slip(1.0, steps=200, nf=1)
+    s4 = _slip(1.0, steps=200, nf=4)
+    assert s4 < 0.6 * s1, (s1, s4)
