@@ -1,0 +1,396 @@
+"""Benchmark of the BTDF-IB/LBM time step on GB300.
+
+Default workload: the paper-scale cylinder case, a 1600 x 800 D2Q9 lattice
+with one cylinder of D = 40 (126 markers) at Re = 200 (tau = 0.53), the
+3-point delta function and the paper's thickness drs = 1.9, FP32 arithmetic
+with FP32 deviation storage.  One step = the IB stage plus the fused
+collide-stream kernel.
+
+Timing: W untimed warm-up steps, then K timed steps.  The lattice (92 MB of
+populations) fits in L2, so L2 is flushed (512 MB write) before every timed
+step and each step is bracketed by its own CUDA events on the launching
+stream; the flush is outside the events.  The fused kernel's duration comes
+from the library's own events around it (profiling mode).
+
+--impl reference times the FP64 CPU oracle on the host cores on the same
+workload (each step one full oracle step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and % of HBM roofline at 1 GB300 (plain vs mixed/batched), Cd error vs FP64"
+BYTES_PER_LU = {0: 72, 1: 36, 2: 36}      # 9 reads + 9 writes of the stored deviation
+L2_FLUSH_BYTES = 512 << 20
+
+
+def workload_case(name):
+    import workloads as W
+    if name == "paper":
+        return W.paper_cylinder(re=200.0, delta=3), \
+            "cylinder 1600x800, D=40, 126 markers, Re=200 (tau=0.53), 3-point delta, drs=1.9"
+    if name == "small":
+        return W.small_cylinder(delta=4), \
+            "cylinder 160x80, D=16, 50 markers, Re=40 (tau=0.56), 4-point delta, drs=2.6"
+    if name == "large":
+        return W.many_cylinders(), \
+            "8192x4096 lattice, 400 cylinders D=20 (63 markers each), Re=200, 3-point delta"
+    raise SystemExit(f"unknown workload {name}")
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def kernel_source_hash():
+    p = os.path.join(ROOT, "paper_1806_09403_gb300", "csrc", "btdf_kernels.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def ncu_traffic(workload, storage):
+    """DRAM bytes per launch of the collide-stream kernel from the committed
+    ncu summary, or None when the summary is missing or was taken on another
+    version of the kernel source."""
+    tag = {0: "f32", 1: "f16", 2: "bf16"}[storage]
+    path = os.path.join(ROOT, "profiles", f"ncu_collide_stream_{workload}_{tag}.txt")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+    t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not h or not t or h.group(1) != kernel_source_hash():
+        return None
+    return float(t.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, period_ms: int = 50):
+        self.idx, self.period = gpu_index, period_ms
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", f"-lms={self.period}"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_oracle_sample(case, seconds, threads, max_steps=None):
+    """Steps the FP64 oracle on the workload until `seconds` have passed."""
+    from oracle import oracle as O
+    O.set_threads(threads)
+    sim = O.Sim.from_case(case)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        sim.step(1)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or (max_steps and n >= max_steps):
+            break
+    return sim, n, el
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def reference_arm(args):
+    """FP64 CPU oracle on the host cores, same workload and metric.  Each step
+    is one full oracle step of the lattice; the arm stops early once
+    --ref-seconds of stepping have passed and reports the steps it ran."""
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    O.build()
+    case, desc = workload_case(args.workload)
+    threads = min(os.cpu_count() or 1, 64)
+    O.set_threads(threads)
+    sim = O.Sim.from_case(case)
+    sim.step(args.warmup if args.warmup <= 10 else 10)
+    t0 = time.perf_counter()
+    done = 0
+    while done < args.steps:
+        sim.step(1)
+        done += 1
+        if time.perf_counter() - t0 > args.ref_seconds:
+            break
+    el = time.perf_counter() - t0
+    v = case.nx * case.ny * done / el / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": 1,
+        "steps": done, "steps_requested": args.steps, "warmup": args.warmup,
+        "ms_per_step": el * 1e3 / done,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": desc, "nx": case.nx, "ny": case.ny, "impl": "FP64 CPU oracle"},
+        "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": threads, "kind": "oracle",
+                         "sample": f"{done} full oracle steps of the workload (time-boxed at "
+                                   f"{args.ref_seconds:.0f} s) after up to 10 warm-up steps"},
+        "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def kernel_mode(args):
+    """Steps the workload with direct launches only (no graphs, flushes or
+    host copies): the program the ncu captures profile."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1806_09403_gb300 import btdf as B
+    case, desc = workload_case(args.workload)
+    storage = {"f32": 0, "f16": 1, "bf16": 2}[args.storage]
+    lat = B.Lattice.from_case(case, storage=storage,
+                              stream=torch.cuda.current_stream().cuda_stream)
+    lat.profile(True)          # direct launches, one event pair per kernel
+    lat.step(args.warmup + args.steps)
+    ms_ib, ms_lbm, n_ib, n_lbm = lat.profile_read()
+    lat.sync()
+    print(json.dumps({"mode": "kernel", "workload": desc, "steps": args.warmup + args.steps,
+                      "ms_lbm_per_launch": ms_lbm / max(n_lbm, 1),
+                      "ms_ib_per_step": ms_ib / max(n_lbm, 1)}))
+    return 0
+
+
+def our_arm(args):
+    import torch
+    world, rank, local = dist_setup(args)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1806_09403_gb300 import btdf as B
+
+    case, desc = workload_case(args.workload)
+    storage = {"f32": 0, "f16": 1, "bf16": 2}[args.storage]
+    stream = torch.cuda.current_stream()
+    lat = B.Lattice.from_case(case, storage=storage, stream=stream.cuda_stream,
+                              history_len=max(args.steps + args.warmup + 64, 4096))
+    nodes = case.nx * case.ny
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    # warm-up (graphs and direct launches both exercised)
+    lat.step(args.warmup)
+    lat.sync()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- timed region: K steps, L2 flushed before each, per-step events ----
+    lat.profile(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            lat.step(1)
+            ev[i][1].record(stream)
+        barrier()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    ms_ib, ms_lbm, n_ib, n_lbm = lat.profile_read()
+    lat.profile(False)
+    lat.sync()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = nodes * args.steps * world / (ms / 1e3) / 1e6
+
+    # ---- roofline of the fused kernel ----
+    peaks = measured_peaks()
+    bpl = BYTES_PER_LU[storage]
+    achieved = bpl * nodes * n_lbm / (ms_lbm / 1e3) / 1e9
+    if peaks and peaks.get("hbm_gbs"):
+        peak, peak_src = float(peaks["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    else:
+        peak, peak_src = 6800.0, "fallback 6.8 TB/s"
+    traffic = ncu_traffic(args.workload, storage)
+
+    # ---- warm sustained rate through CUDA graphs (no flush) ----
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nwarm = 2048
+    lat.step(64)
+    e0.record(stream)
+    lat.step(nwarm)
+    e1.record(stream)
+    lat.sync()
+    warm = nodes * nwarm / (e0.elapsed_time(e1) / 1e3) / 1e6
+
+    # ---- end to end through the C ABI with host buffers ----
+    nb = len(case.bodies[0].X) if case.bodies else 0
+    ubx = np.zeros(nb)
+    uby = np.zeros(nb)
+    fx = np.zeros(1)
+    fy = np.zeros(1)
+    ne2e = min(args.steps, 2000)
+    tot = 0.0
+    barrier()
+    for i in range(ne2e):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if nb:
+            lat.set_marker_velocity(0, ubx, uby)           # H2D of the step's input
+        lat.step(1)
+        if nb:
+            lat.forces(0, lat.steps - 1, 1, out=(fx, fy))  # D2H of the step's result
+        else:
+            lat.sync()
+        tot += time.perf_counter() - t0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([tot], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot = float(t.item())
+    e2e = nodes * ne2e * world / tot / 1e6
+
+    # ---- FP64 oracle on the host cores, and drag error against it ----
+    cpu = None
+    cd_err = None
+    if rank == 0 and not args.no_cpu_baseline:
+        threads = min(os.cpu_count() or 1, 64)
+        sim, n_or, el = run_oracle_sample(case, args.cpu_seconds, threads)
+        cpu = {"value": nodes * n_or / el / 1e6, "unit": "MLUPS", "cores": threads,
+               "kind": "oracle",
+               "sample": f"first {n_or} steps of the same workload ({el:.1f} s of CPU time, "
+                         f"OpenMP over rows)"}
+        if case.bodies:
+            ref = B.Lattice.from_case(case, storage=storage, stream=stream.cuda_stream,
+                                      history_len=max(n_or, 16))
+            ref.step(n_or)
+            gx, _ = ref.forces(0, 0, n_or)
+            rx, _ = sim.history(0, 0, n_or)
+            cd_err = float(np.max(np.abs(gx - rx) / np.maximum(np.abs(rx), np.abs(rx).mean())))
+            ref.close()
+
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {0: "f32", 1: "f32 (f16 storage)", 2: "f32 (bf16 storage)"}[storage],
+        "data": "synthetic",
+        "config": {"workload": desc, "nx": case.nx, "ny": case.ny,
+                   "storage": args.storage, "markers": sum(len(b.X) for b in case.bodies),
+                   "l2": "flushed (512 MB write) before every timed step; flush outside the "
+                         "per-step CUDA events",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "collide_stream", "bytes_per_lu": bpl,
+                     "kernel_ms_per_launch": ms_lbm / max(n_lbm, 1),
+                     "ib_ms_per_step": ms_ib / max(n_lbm, 1), "peak_source": peak_src},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e, "unit": "MLUPS", "h2d_bytes_per_step": 16 * nb,
+                "d2h_bytes_per_step": 16 if nb else 0,
+                "how": "per step: marker velocities H2D, one step, body force D2H, synchronous"},
+        "gpu_launches": int(n_ib + n_lbm),
+        "clocks": clk.summary(),
+        "graph_warm_mlups": warm,
+        "cd_err_vs_fp64": cd_err,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="paper", choices=["paper", "small", "large"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--ref-seconds", type=float, default=90.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="bench", choices=["bench", "kernel"])
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        return reference_arm(args)
+    if args.mode == "kernel":
+        return kernel_mode(args)
+    return our_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

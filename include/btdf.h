@@ -1,0 +1,189 @@
+/* btdf.h - C ABI of the GB300 (sm_103a) implementation of the boundary
+ * thickening direct-forcing immersed-boundary lattice Boltzmann method
+ * (BTDF-IB/LBM) of M. Jiang and Z. Liu, arXiv 1806.09403.
+ *
+ * One call of btdf_step advances the flow by whole time steps of the paper's
+ * Algorithm 1 (with NF forcing passes):
+ *   IB stage   - density and unforced velocity at the marker supports
+ *                (Eqs. 9-10), interpolation to the Lagrangian markers with the
+ *                regularized delta function (Eqs. 12, 14, 37-39), the explicit
+ *                direct-forcing force F_b = 2 rho (U_b - D_I u*) (Eq. 20) and
+ *                the force on each body (Eq. 27), reduced in FP64.
+ *   LBM stage  - spreading of F_b with the thickened solid shell drs
+ *                (Eqs. 13, 15), velocity correction u = u* + f / (2 rho)
+ *                (Eq. 11), BGK collision with the Guo forcing term
+ *                (Eqs. 5-7) and streaming, fused in one kernel.
+ *
+ * Units: lattice units, dh = dt = c = 1, reference density rho0 = 1.
+ * Fields: row-major, x fastest, node (x, y) at integer coordinates
+ * 0..nx-1, 0..ny-1.  D2Q9 population order (Eq. 8):
+ *   0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1).
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns a btdf_status (0 on success, < 0 on error);
+ *     btdf_last_error() gives a message for the last failure of a context.
+ *   - The caller owns every pointer it passes; the library copies what it
+ *     needs and never frees or retains caller memory.  Pointers are host
+ *     pointers unless stated otherwise.
+ *   - A context owns the device memory it allocates and frees it in
+ *     btdf_destroy.  All device work is issued on the stream given to
+ *     btdf_create; calls that return data to the host synchronize it.
+ *   - A context is not thread-safe: serialize calls on one context.
+ *   - Device-side failures (an unstable density at a marker, a bounded wait
+ *     that gave up) are recorded in a status word and reported by the next
+ *     btdf_sync or read call, and are sticky.
+ */
+#ifndef BTDF_H
+#define BTDF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct btdf_ctx btdf_ctx;
+
+typedef enum {
+    BTDF_OK = 0,
+    BTDF_EINVAL = -1,     /* bad argument or configuration */
+    BTDF_ENOMEM = -2,     /* device or host allocation failed */
+    BTDF_ECUDA = -3,      /* a CUDA runtime call failed (message in last_error) */
+    BTDF_EUNSTABLE = -4,  /* non-positive or non-finite density/force at a marker */
+    BTDF_ETIMEOUT = -5,   /* a bounded device wait gave up */
+    BTDF_ESTATE = -6      /* call not valid in the current state (e.g. no fields) */
+} btdf_status;
+
+/* Regularized delta functions of Sec. 4.3: 2-point (Eq. 37), 3-point (Eq. 38),
+ * 4-point (Eq. 39), and a 4-point cosine kernel that the paper does not print. */
+typedef enum {
+    BTDF_DELTA2 = 2,
+    BTDF_DELTA3 = 3,
+    BTDF_DELTA4 = 4,
+    BTDF_DELTA4COS = 5
+} btdf_delta;
+
+/* Population storage.  All forms store deviations f - w_a from the lattice
+ * weights; arithmetic is FP32 in every form. */
+typedef enum {
+    BTDF_F32 = 0,
+    BTDF_F16DEV = 1,
+    BTDF_BF16DEV = 2
+} btdf_storage;
+
+/* x boundaries: periodic, or inlet at x = 0 (non-equilibrium extrapolation to
+ * velocity (u_in, 0)) with a zero-gradient outlet at x = nx-1. */
+typedef enum { BTDF_BCX_PERIODIC = 0, BTDF_BCX_INOUT = 1 } btdf_bc_x;
+/* y boundaries: periodic, free-slip walls (half-way specular reflection) or
+ * no-slip walls (half-way bounce-back); walls sit half a node outside rows
+ * 0 and ny-1. */
+typedef enum { BTDF_BCY_PERIODIC = 0, BTDF_BCY_FREESLIP = 1, BTDF_BCY_NOSLIP = 2 } btdf_bc_y;
+
+typedef enum {
+    BTDF_FIELD_RHO = 0,   /* density, Eq. 9 (ny*nx floats) */
+    BTDF_FIELD_UX = 1,    /* unforced velocity u*, Eq. 10 (ny*nx floats) */
+    BTDF_FIELD_UY = 2,
+    BTDF_FIELD_POPS = 3   /* populations f (not deviations), [9][ny][nx] floats */
+} btdf_field;
+
+typedef struct {
+    int32_t nx, ny;        /* lattice size, >= 4 each */
+    double tau;            /* BGK relaxation time, > 0.5 (tau = 0.5 + 3 nu) */
+    double u_in;           /* inlet speed for BTDF_BCX_INOUT */
+    int32_t delta;         /* btdf_delta */
+    int32_t nf;            /* forcing passes per step, 1 = BTDF/DF, > 1 = MDF (Sec. 3.2) */
+    int32_t storage;       /* btdf_storage */
+    int32_t bc_x, bc_y;    /* btdf_bc_x, btdf_bc_y */
+    int32_t history_len;   /* steps of body-force history kept on the device (>= 1) */
+    double gx, gy;         /* uniform body force added to the IB force everywhere */
+} btdf_config;
+
+/* Fills *cfg with a 64 x 64 periodic FP32 lattice, tau = 0.6, 3-point delta,
+ * nf = 1, history_len = 4096. */
+int btdf_config_default(btdf_config *cfg);
+
+/* Validates *cfg, allocates the two population buffers and per-context
+ * scratch on the device, and binds the context to `stream` (a cudaStream_t;
+ * NULL = the legacy default stream).  On success *out receives the context.
+ * Errors: EINVAL (bad configuration; nothing allocated), ENOMEM, ECUDA. */
+int btdf_create(const btdf_config *cfg, void *stream, btdf_ctx **out);
+int btdf_destroy(btdf_ctx *ctx);
+
+/* Sets f = f_eq(rho, u) at every node (Eq. 6).  rho, ux, uy are host arrays
+ * of ny*nx doubles.  Resets the step counter and the force history. */
+int btdf_init_fields(btdf_ctx *ctx, const double *rho, const double *ux, const double *uy);
+
+/* Adds one rigid body of n markers at (X[l], Y[l]) with prescribed velocity
+ * (Ubx[l], Uby[l]) (NULL = at rest), arc length ds per marker and solid-shell
+ * thickness drs (Eq. 15; drs <= 0 takes the value suggested in Sec. 4.4 for
+ * the configured delta: 1.4, 1.9, 2.6 for 2, 3, 4 points, 2.6 for the cosine
+ * kernel).  Interpolation weights delta(x_e - X) delta(y_e - Y) (Eq. 14) are
+ * evaluated once here in FP64; markers are static.  Every marker's support
+ * must lie at least partly inside the lattice.  *body_id receives the index.
+ * Errors: EINVAL (n < 1, ds <= 0, marker outside the lattice). */
+int btdf_add_markers(btdf_ctx *ctx, int32_t n, const double *X, const double *Y,
+                     const double *Ubx, const double *Uby, double ds, double drs,
+                     int32_t *body_id);
+
+/* Replaces the prescribed marker velocities U_b of one body (host arrays of
+ * that body's marker count).  Asynchronous on the context stream. */
+int btdf_set_marker_velocity(btdf_ctx *ctx, int32_t body, const double *Ubx, const double *Uby);
+
+/* Advances nsteps time steps (Algorithm 1), asynchronously on the context
+ * stream.  Requires btdf_init_fields or btdf_load_state first (ESTATE). */
+int btdf_step(btdf_ctx *ctx, int64_t nsteps);
+
+/* Waits for the context stream and returns the sticky device status
+ * (OK, EUNSTABLE or ETIMEOUT). */
+int btdf_sync(btdf_ctx *ctx);
+
+/* Force on one body (Eq. 27, force exerted by the fluid on the body) for the
+ * steps first .. first+n-1, into host arrays Fx, Fy of n doubles.  The steps
+ * must have been taken and must still be inside the device history ring.
+ * Synchronizes.  Errors: EINVAL (body or step range). */
+int btdf_read_forces(btdf_ctx *ctx, int32_t body, int64_t first, int64_t n,
+                     double *Fx, double *Fy);
+
+/* Per-marker results of the last step for one body, host arrays of the body's
+ * marker count (any may be NULL): interpolated unforced velocity D_I u*
+ * (Eq. 14) and the Lagrangian force F_b summed over the forcing passes
+ * (Eq. 20). Synchronizes. */
+int btdf_read_markers(btdf_ctx *ctx, int32_t body, float *Usx, float *Usy,
+                      float *Fbx, float *Fby);
+
+/* Macroscopic field or populations of the current state (after the last
+ * step's streaming and boundary rules), as floats.  dst is a host pointer, or
+ * a device pointer when dst_is_device != 0.  Synchronizes. */
+int btdf_read_field(btdf_ctx *ctx, int32_t kind, float *dst, int32_t dst_is_device);
+
+int64_t btdf_step_count(const btdf_ctx *ctx);
+
+/* Checkpoint of the populations and the step counter (not the force
+ * history).  btdf_state_size gives the byte count; save copies to a host
+ * buffer of at least that size; load restores a checkpoint of a context with
+ * the same nx, ny and storage.  Errors: EINVAL (size or shape mismatch). */
+int btdf_state_size(btdf_ctx *ctx, size_t *bytes);
+int btdf_save_state(btdf_ctx *ctx, void *dst, size_t cap, size_t *used);
+int btdf_load_state(btdf_ctx *ctx, const void *src, size_t len);
+
+/* Profiling hooks for benchmarks: while enabled, btdf_step launches every
+ * kernel directly (no CUDA graph) between CUDA events on the context stream;
+ * btdf_profile_read synchronizes and returns the summed device time of the
+ * IB-stage kernels and of the fused collide-stream kernel, and the number of
+ * kernel launches, since profiling was enabled.  Enabling resets the sums. */
+int btdf_profile_enable(btdf_ctx *ctx, int32_t on);
+int btdf_profile_read(btdf_ctx *ctx, double *ms_ib, double *ms_lbm, int64_t *launches_ib,
+                      int64_t *launches_lbm);
+
+/* Bytes of device memory the context holds. */
+int btdf_device_bytes(const btdf_ctx *ctx, size_t *bytes);
+
+const char *btdf_last_error(const btdf_ctx *ctx);
+const char *btdf_status_string(int status);
+int btdf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BTDF_H */

@@ -1,0 +1,259 @@
+"""Thin ctypes binding of the C ABI in ``include/btdf.h``.
+
+Argument marshalling only: every step of the method runs in the CUDA library
+``_lib/libbtdf.so``.  There is no CPU fallback: if the library is missing or
+cannot be loaded, importing the binding raises.
+
+The raw entry points keep their C names (``btdf_create``, ``btdf_step``, ...);
+``Lattice`` wraps one context for numpy / torch callers.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Tuple
+
+import numpy as np
+
+from . import _build
+
+BTDF_OK, BTDF_EINVAL, BTDF_ENOMEM, BTDF_ECUDA, BTDF_EUNSTABLE, BTDF_ETIMEOUT, BTDF_ESTATE = \
+    0, -1, -2, -3, -4, -5, -6
+BTDF_F32, BTDF_F16DEV, BTDF_BF16DEV = 0, 1, 2
+BTDF_BCX_PERIODIC, BTDF_BCX_INOUT = 0, 1
+BTDF_BCY_PERIODIC, BTDF_BCY_FREESLIP, BTDF_BCY_NOSLIP = 0, 1, 2
+FIELD_RHO, FIELD_UX, FIELD_UY, FIELD_POPS = 0, 1, 2, 3
+
+# Every symbol include/btdf.h declares.
+EXPORTS = [
+    "btdf_config_default", "btdf_create", "btdf_destroy", "btdf_init_fields",
+    "btdf_add_markers", "btdf_set_marker_velocity", "btdf_step", "btdf_sync",
+    "btdf_read_forces", "btdf_read_markers", "btdf_read_field", "btdf_step_count",
+    "btdf_state_size", "btdf_save_state", "btdf_load_state", "btdf_profile_enable",
+    "btdf_profile_read", "btdf_device_bytes", "btdf_last_error", "btdf_status_string",
+    "btdf_version",
+]
+
+
+class btdf_config(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int32), ("ny", C.c_int32),
+        ("tau", C.c_double), ("u_in", C.c_double),
+        ("delta", C.c_int32), ("nf", C.c_int32), ("storage", C.c_int32),
+        ("bc_x", C.c_int32), ("bc_y", C.c_int32), ("history_len", C.c_int32),
+        ("gx", C.c_double), ("gy", C.c_double),
+    ]
+
+
+class BtdfError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+_lib: Optional[C.CDLL] = None
+_dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+
+
+def lib() -> C.CDLL:
+    """Loads the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise ImportError(f"libbtdf.so is not built ({path}); run __graft_entry__.build()")
+    L = C.CDLL(path)
+    vp = C.c_void_p
+    ctxp = C.c_void_p
+    L.btdf_config_default.argtypes = [C.POINTER(btdf_config)]
+    L.btdf_create.argtypes = [C.POINTER(btdf_config), vp, C.POINTER(ctxp)]
+    L.btdf_destroy.argtypes = [ctxp]
+    L.btdf_init_fields.argtypes = [ctxp, _dp, _dp, _dp]
+    L.btdf_add_markers.argtypes = [ctxp, C.c_int32, _dp, _dp, vp, vp, C.c_double, C.c_double,
+                                   C.POINTER(C.c_int32)]
+    L.btdf_set_marker_velocity.argtypes = [ctxp, C.c_int32, _dp, _dp]
+    L.btdf_step.argtypes = [ctxp, C.c_int64]
+    L.btdf_sync.argtypes = [ctxp]
+    L.btdf_read_forces.argtypes = [ctxp, C.c_int32, C.c_int64, C.c_int64, vp, vp]
+    L.btdf_read_markers.argtypes = [ctxp, C.c_int32, vp, vp, vp, vp]
+    L.btdf_read_field.argtypes = [ctxp, C.c_int32, vp, C.c_int32]
+    L.btdf_step_count.argtypes = [ctxp]
+    L.btdf_step_count.restype = C.c_int64
+    L.btdf_state_size.argtypes = [ctxp, C.POINTER(C.c_size_t)]
+    L.btdf_save_state.argtypes = [ctxp, vp, C.c_size_t, C.POINTER(C.c_size_t)]
+    L.btdf_load_state.argtypes = [ctxp, vp, C.c_size_t]
+    L.btdf_profile_enable.argtypes = [ctxp, C.c_int32]
+    L.btdf_profile_read.argtypes = [ctxp, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                    C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+    L.btdf_device_bytes.argtypes = [ctxp, C.POINTER(C.c_size_t)]
+    L.btdf_last_error.argtypes = [ctxp]
+    L.btdf_last_error.restype = C.c_char_p
+    L.btdf_status_string.argtypes = [C.c_int]
+    L.btdf_status_string.restype = C.c_char_p
+    L.btdf_version.restype = C.c_int
+    _lib = L
+    return L
+
+
+# ---- raw entry points with the C names -----------------------------------------
+
+def btdf_config_default() -> btdf_config:
+    cfg = btdf_config()
+    lib().btdf_config_default(C.byref(cfg))
+    return cfg
+
+
+def btdf_create(cfg: btdf_config, stream: int = 0) -> Tuple[int, Optional[int]]:
+    out = C.c_void_p()
+    rc = lib().btdf_create(C.byref(cfg), C.c_void_p(stream or None), C.byref(out))
+    return rc, out.value
+
+
+def btdf_status_string(rc: int) -> str:
+    return lib().btdf_status_string(rc).decode()
+
+
+def btdf_version() -> int:
+    return lib().btdf_version()
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64).ravel()
+
+
+class Lattice:
+    """One BTDF-IB/LBM context.  Fields are (ny, nx) arrays, x fastest."""
+
+    def __init__(self, nx, ny, tau, u_in=0.0, delta=3, nf=1, storage=BTDF_F32,
+                 bc_x=BTDF_BCX_PERIODIC, bc_y=BTDF_BCY_PERIODIC, gx=0.0, gy=0.0,
+                 history_len=4096, stream: int = 0):
+        cfg = btdf_config_default()
+        cfg.nx, cfg.ny, cfg.tau, cfg.u_in = int(nx), int(ny), float(tau), float(u_in)
+        cfg.delta, cfg.nf, cfg.storage = int(delta), int(nf), int(storage)
+        cfg.bc_x, cfg.bc_y, cfg.history_len = int(bc_x), int(bc_y), int(history_len)
+        cfg.gx, cfg.gy = float(gx), float(gy)
+        self.cfg = cfg
+        self.nx, self.ny = int(nx), int(ny)
+        rc, ctx = btdf_create(cfg, stream)
+        if rc != BTDF_OK:
+            raise BtdfError(rc, f"btdf_create: {btdf_status_string(rc)}")
+        self._ctx = ctx
+        self.body_markers = []
+
+    @classmethod
+    def from_case(cls, case, storage=BTDF_F32, stream: int = 0, history_len=4096, drs=None):
+        lat = cls(case.nx, case.ny, case.tau, case.u_in, case.delta, case.nf, storage,
+                  case.bc_x, case.bc_y, case.gx, case.gy, history_len, stream)
+        lat.init_fields(*case.initial_fields())
+        for b in case.bodies:
+            lat.add_markers(b.X, b.Y, b.ds, b.Ubx, b.Uby, drs=case.drs if drs is None else drs)
+        return lat
+
+    def _check(self, rc: int, what: str):
+        if rc != BTDF_OK:
+            msg = lib().btdf_last_error(self._ctx).decode()
+            raise BtdfError(rc, f"{what}: {btdf_status_string(rc)}: {msg}")
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            lib().btdf_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_fields(self, rho, ux, uy):
+        self._check(lib().btdf_init_fields(self._ctx, _f64(rho), _f64(ux), _f64(uy)),
+                    "btdf_init_fields")
+
+    def add_markers(self, X, Y, ds, Ubx=None, Uby=None, drs=0.0) -> int:
+        X, Y = _f64(X), _f64(Y)
+        n = len(X)
+        ubx = None if Ubx is None else _f64(Ubx)
+        uby = None if Uby is None else _f64(Uby)
+        bid = C.c_int32(-1)
+        rc = lib().btdf_add_markers(self._ctx, n, X, Y,
+                                    None if ubx is None else ubx.ctypes.data,
+                                    None if uby is None else uby.ctypes.data,
+                                    float(ds), float(drs or 0.0), C.byref(bid))
+        self._check(rc, "btdf_add_markers")
+        self.body_markers.append(n)
+        return bid.value
+
+    def set_marker_velocity(self, body, Ubx, Uby):
+        self._check(lib().btdf_set_marker_velocity(self._ctx, body, _f64(Ubx), _f64(Uby)),
+                    "btdf_set_marker_velocity")
+
+    def step(self, n=1):
+        self._check(lib().btdf_step(self._ctx, int(n)), "btdf_step")
+
+    def sync(self):
+        self._check(lib().btdf_sync(self._ctx), "btdf_sync")
+
+    @property
+    def steps(self) -> int:
+        return lib().btdf_step_count(self._ctx)
+
+    def forces(self, body=0, first=0, n=None, out=None):
+        n = self.steps - first if n is None else n
+        if out is None:
+            out = (np.zeros(n), np.zeros(n))
+        Fx, Fy = out
+        self._check(lib().btdf_read_forces(self._ctx, body, first, n, Fx.ctypes.data,
+                                           Fy.ctypes.data), "btdf_read_forces")
+        return Fx, Fy
+
+    def markers(self, body=0):
+        n = self.body_markers[body]
+        a = [np.zeros(n, dtype=np.float32) for _ in range(4)]
+        self._check(lib().btdf_read_markers(self._ctx, body, *[x.ctypes.data for x in a]),
+                    "btdf_read_markers")
+        return dict(zip(["Usx", "Usy", "Fbx", "Fby"], a))
+
+    def field(self, kind):
+        shape = (9, self.ny, self.nx) if kind == FIELD_POPS else (self.ny, self.nx)
+        out = np.zeros(shape, dtype=np.float32)
+        self._check(lib().btdf_read_field(self._ctx, kind, out.ctypes.data, 0), "btdf_read_field")
+        return out
+
+    def field_to_device(self, kind, ptr: int):
+        self._check(lib().btdf_read_field(self._ctx, kind, ptr, 1), "btdf_read_field")
+
+    def moments(self):
+        return self.field(FIELD_RHO), self.field(FIELD_UX), self.field(FIELD_UY)
+
+    def save_state(self) -> bytes:
+        n = C.c_size_t()
+        self._check(lib().btdf_state_size(self._ctx, C.byref(n)), "btdf_state_size")
+        buf = (C.c_char * n.value)()
+        used = C.c_size_t()
+        self._check(lib().btdf_save_state(self._ctx, buf, n.value, C.byref(used)),
+                    "btdf_save_state")
+        return bytes(buf)
+
+    def load_state(self, blob: bytes):
+        buf = C.create_string_buffer(blob, len(blob))
+        self._check(lib().btdf_load_state(self._ctx, buf, len(blob)), "btdf_load_state")
+
+    def profile(self, on: bool):
+        self._check(lib().btdf_profile_enable(self._ctx, 1 if on else 0), "btdf_profile_enable")
+
+    def profile_read(self):
+        a, b = C.c_double(), C.c_double()
+        la, lb = C.c_int64(), C.c_int64()
+        self._check(lib().btdf_profile_read(self._ctx, C.byref(a), C.byref(b), C.byref(la),
+                                            C.byref(lb)), "btdf_profile_read")
+        return a.value, b.value, la.value, lb.value
+
+    def device_bytes(self) -> int:
+        n = C.c_size_t()
+        self._check(lib().btdf_device_bytes(self._ctx, C.byref(n)), "btdf_device_bytes")
+        return n.value

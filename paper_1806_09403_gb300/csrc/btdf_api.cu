@@ -1,0 +1,796 @@
+// btdf_api.cu - host side of the C ABI declared in include/btdf.h.
+//
+// Holds the context, validates configurations, evaluates the static marker
+// weights in FP64 (Eq. 14 with the delta functions of Eqs. 37-39), builds the
+// node-centric spreading table (Eq. 15), orders the kernels of a time step
+// (Algorithm 1) and replays them through CUDA graphs.
+#include "btdf.h"
+#include "btdf_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace btdf;
+
+namespace {
+
+constexpr int kGraphSteps = 64;          // steps per replayed CUDA graph (even)
+constexpr uint64_t kStateMagic = 0x3130465444544242ull;
+
+struct Body {
+    int first = 0, n = 0;
+    double ds = 0.0, drs = 0.0;
+    std::vector<double> X, Y, Ubx, Uby;
+    std::vector<double> wsum;      // sum of each marker's weights (filled by rebuild)
+};
+
+struct StateHeader {
+    uint64_t magic;
+    int32_t nx, ny, nxp, storage;
+    int32_t poststream, reserved;
+    int64_t steps;
+};
+
+// Regularized delta functions of Sec. 4.3 evaluated in FP64 on the host.
+double delta_fn(int kind, double r) {
+    const double a = std::fabs(r);
+    switch (kind) {
+    case 2:  // Eq. 37
+        return a <= 1.0 ? 1.0 - a : 0.0;
+    case 3:  // Eq. 38
+        if (a > 1.5) return 0.0;
+        if (a > 0.5) return (5.0 - 3.0 * a - std::sqrt(1.0 - 3.0 * (1.0 - a) * (1.0 - a))) / 6.0;
+        return (1.0 + std::sqrt(1.0 - 3.0 * a * a)) / 3.0;
+    case 4:  // Eq. 39
+        if (a >= 2.0) return 0.0;
+        if (a >= 1.0) return (5.0 - 2.0 * a - std::sqrt(-7.0 + 12.0 * a - 4.0 * a * a)) / 8.0;
+        return (3.0 - 2.0 * a + std::sqrt(1.0 + 4.0 * a - 4.0 * a * a)) / 8.0;
+    case 5:  // cosine kernel with 4-point support
+        return a < 2.0 ? 0.25 * (1.0 + std::cos(M_PI * a * 0.5)) : 0.0;
+    default:
+        return 0.0;
+    }
+}
+
+int support_width(int kind) { return kind == 2 ? 2 : kind == 3 ? 3 : (kind == 4 || kind == 5) ? 4 : 0; }
+
+// Solid-shell thickness drs/dh suggested in Sec. 4.4 (the cosine kernel has
+// the 4-point support and takes the 4-point value).
+double paper_drs(int kind) { return kind == 2 ? 1.4 : kind == 3 ? 1.9 : 2.6; }
+
+size_t elem_bytes(int storage) { return storage == kStoreF32 ? 4 : 2; }
+
+}  // namespace
+
+struct btdf_ctx {
+    btdf_config cfg{};
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;
+    int nxp = 0, nseg = 0, width = 0;
+    long long plane = 0;
+    size_t elem = 4;
+    void* g[2] = {nullptr, nullptr};
+    int cur = 0;
+    bool poststream = true;
+    bool has_fields = false;
+    int64_t steps = 0;
+    int64_t hist_from = 0;
+
+    std::vector<Body> bodies;
+    int nmark = 0, nband = 0;
+    Marker* d_mk = nullptr;
+    MarkerAux* d_aux = nullptr;
+    float2* d_F[2] = {nullptr, nullptr};
+    float2* d_Us = nullptr;
+    float* d_rhol = nullptr;
+    int* d_seg_index = nullptr;
+    int* d_seg_ptr = nullptr;
+    CsrEntry* d_csr = nullptr;
+    int* d_body_ptr = nullptr;
+    double* d_body_scale = nullptr;
+    double2* d_hist = nullptr;
+    unsigned long long* d_step = nullptr;
+    unsigned int* d_ticket = nullptr;
+    int* d_status = nullptr;
+    std::vector<MarkerAux> aux_host;
+
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;         // 3 per profiled step
+    size_t ev_used = 0;
+
+    size_t dev_bytes = 0;
+    size_t marker_bytes = 0;           // part of dev_bytes held by marker data
+    std::string err;
+};
+
+namespace {
+
+int fail(btdf_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+int cuda_fail(btdf_ctx* c, cudaError_t e, const char* where) {
+    return fail(c, BTDF_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);   \
+    } while (0)
+
+template <typename P>
+cudaError_t dalloc(btdf_ctx* ctx, P** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) return cudaSuccess;
+    cudaError_t e = cudaMalloc((void**)p, bytes);
+    if (e == cudaSuccess) ctx->dev_bytes += bytes;
+    else cudaGetLastError();   // allocation errors are not sticky; clear them
+    return e;
+}
+
+template <typename P>
+void dfree(btdf_ctx* ctx, P*& p) {
+    (void)ctx;
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+void drop_graphs(btdf_ctx* ctx) {
+    for (auto& g : ctx->gexec)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
+void free_markers(btdf_ctx* ctx) {
+    ctx->dev_bytes -= ctx->marker_bytes;
+    ctx->marker_bytes = 0;
+    dfree(ctx, ctx->d_mk);
+    dfree(ctx, ctx->d_aux);
+    dfree(ctx, ctx->d_F[0]);
+    dfree(ctx, ctx->d_F[1]);
+    dfree(ctx, ctx->d_Us);
+    dfree(ctx, ctx->d_rhol);
+    dfree(ctx, ctx->d_seg_index);
+    dfree(ctx, ctx->d_seg_ptr);
+    dfree(ctx, ctx->d_csr);
+    dfree(ctx, ctx->d_body_ptr);
+    dfree(ctx, ctx->d_body_scale);
+    dfree(ctx, ctx->d_hist);
+}
+
+LatticeParams lattice_params(const btdf_ctx* ctx) {
+    LatticeParams p{};
+    p.nx = ctx->cfg.nx;
+    p.ny = ctx->cfg.ny;
+    p.nxp = ctx->nxp;
+    p.nseg = ctx->nseg;
+    p.plane = ctx->plane;
+    p.bcx = ctx->cfg.bc_x;
+    p.bcy = ctx->cfg.bc_y;
+    p.omega = (float)(1.0 / ctx->cfg.tau);
+    p.guo = (float)(1.0 - 0.5 / ctx->cfg.tau);
+    p.u_in = (float)ctx->cfg.u_in;
+    p.urx = (float)ctx->cfg.u_in;   // reference velocity of the stored deviations
+    p.ury = 0.0f;
+    p.gx = (float)ctx->cfg.gx;
+    p.gy = (float)ctx->cfg.gy;
+    p.seg_index = ctx->nmark > 0 ? ctx->d_seg_index : nullptr;
+    p.seg_ptr = ctx->d_seg_ptr;
+    p.csr = ctx->d_csr;
+    p.F = ctx->d_F[(ctx->cfg.nf - 1) % 2];
+    p.step = ctx->d_step;
+    return p;
+}
+
+cudaEvent_t next_event(btdf_ctx* ctx) {
+    if (ctx->ev_used == ctx->ev.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        ctx->ev.push_back(e);
+    }
+    return ctx->ev[ctx->ev_used++];
+}
+
+// Issues the kernels of one time step reading buffer `cur` (Algorithm 1).
+int enqueue_step(btdf_ctx* ctx, cudaStream_t st, bool pull, int cur, bool prof) {
+    const LatticeParams p = lattice_params(ctx);
+    cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+    if (prof) {
+        e0 = next_event(ctx);
+        e1 = next_event(ctx);
+        e2 = next_event(ctx);
+        if (!e0 || !e1 || !e2) return fail(ctx, BTDF_ECUDA, "cudaEventCreate failed");
+        CK(cudaEventRecord(e0, st));
+    }
+    if (ctx->nmark > 0) {
+        for (int k = 1; k <= ctx->cfg.nf; k++) {
+            IbParams q{};
+            q.nmark = ctx->nmark;
+            q.nbody = (int)ctx->bodies.size();
+            q.mk = ctx->d_mk;
+            q.aux = ctx->d_aux;
+            q.F_prev = k == 1 ? nullptr : ctx->d_F[(k - 2) % 2];
+            q.F_out = ctx->d_F[(k - 1) % 2];
+            q.Us = ctx->d_Us;
+            q.rhol = ctx->d_rhol;
+            q.first_pass = k == 1;
+            q.last_pass = k == ctx->cfg.nf;
+            q.body_ptr = ctx->d_body_ptr;
+            q.body_scale = ctx->d_body_scale;
+            q.hist = ctx->d_hist;
+            q.hist_len = ctx->cfg.history_len;
+            q.step = ctx->d_step;
+            q.ticket = ctx->d_ticket;
+            q.status = ctx->d_status;
+            CK(launch_ib_force(ctx->cfg.storage, pull, ctx->width, ctx->g[cur], p, q, st));
+        }
+    }
+    if (prof) CK(cudaEventRecord(e1, st));
+    CK(launch_collide_stream(ctx->cfg.storage, pull, ctx->g[cur], ctx->g[1 - cur], p, st));
+    if (prof) CK(cudaEventRecord(e2, st));
+    return BTDF_OK;
+}
+
+int ensure_graph(btdf_ctx* ctx, int cur) {
+    if (ctx->gexec[cur]) return BTDF_OK;
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
+    int rc = BTDF_OK;
+    int c = cur;
+    for (int i = 0; i < kGraphSteps && rc == BTDF_OK; i++) {
+        rc = enqueue_step(ctx, ctx->cap, true, c, false);
+        c = 1 - c;
+    }
+    cudaError_t e = cudaStreamEndCapture(ctx->cap, &graph);
+    if (rc != BTDF_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&ctx->gexec[cur], graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
+    return BTDF_OK;
+}
+
+int read_status(btdf_ctx* ctx) {
+    int st = 0;
+    CK(cudaMemcpyAsync(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (st & kStatusTimeout) return fail(ctx, BTDF_ETIMEOUT, "a bounded device wait gave up");
+    if (st & kStatusUnstable)
+        return fail(ctx, BTDF_EUNSTABLE, "non-positive or non-finite density or force at a marker");
+    return BTDF_OK;
+}
+
+// Static marker data and the node-centric spreading table (Eqs. 14, 15).
+int rebuild_markers(btdf_ctx* ctx) {
+    drop_graphs(ctx);
+    free_markers(ctx);
+    const int nx = ctx->cfg.nx, ny = ctx->cfg.ny, S = ctx->width;
+    const bool px = ctx->cfg.bc_x == kBcxPeriodic, py = ctx->cfg.bc_y == kBcyPeriodic;
+    const int nm = ctx->nmark, nb = (int)ctx->bodies.size();
+    if (nm == 0) return BTDF_OK;
+    std::vector<Marker> mk(nm);
+    struct Ent { long long node; int marker; double w; };
+    std::vector<Ent> ents;
+    ents.reserve((size_t)nm * S * S);
+    std::vector<int> body_ptr(nb + 1);
+    std::vector<double> scale(nb);
+    ctx->aux_host.assign(nm, MarkerAux{});
+    for (int b = 0; b < nb; b++) {
+        Body& B = ctx->bodies[b];
+        B.wsum.assign(B.n, 0.0);
+        body_ptr[b] = B.first;
+        body_ptr[b + 1] = B.first + B.n;
+        scale[b] = B.ds * B.drs;
+        for (int l = 0; l < B.n; l++) {
+            const int m = B.first + l;
+            const double X = B.X[l], Y = B.Y[l];
+            const int i0 = (int)std::floor(X - 0.5 * S) + 1;   // first node with x > X - S/2
+            const int j0 = (int)std::floor(Y - 0.5 * S) + 1;
+            double wx[4] = {0, 0, 0, 0}, wy[4] = {0, 0, 0, 0};
+            bool okx[4] = {false, false, false, false}, oky[4] = {false, false, false, false};
+            Marker& M = mk[m];
+            for (int i = 0; i < 4; i++) {
+                M.xs[i] = 0;
+                M.ys[i] = 0;
+            }
+            for (int i = 0; i < S; i++) {
+                int x = i0 + i, y = j0 + i;
+                wx[i] = delta_fn(ctx->cfg.delta, (double)x - X);
+                wy[i] = delta_fn(ctx->cfg.delta, (double)y - Y);
+                if (px) x = ((x % nx) + nx) % nx;
+                if (py) y = ((y % ny) + ny) % ny;
+                okx[i] = x >= 0 && x < nx;
+                oky[i] = y >= 0 && y < ny;
+                M.xs[i] = std::min(std::max(x, 0), nx - 1);
+                M.ys[i] = std::min(std::max(y, 0), ny - 1);
+            }
+            for (int k = 0; k < 16; k++) M.w[k] = 0.0f;
+            for (int j = 0; j < S; j++)
+                for (int i = 0; i < S; i++) {
+                    if (!okx[i] || !oky[j]) continue;
+                    const double w = wx[i] * wy[j];
+                    M.w[j * S + i] = (float)w;
+                    B.wsum[l] += w;
+                    if (w != 0.0)
+                        ents.push_back({(long long)M.ys[j] * nx + M.xs[i], m, w * B.drs * B.ds});
+                }
+            MarkerAux& A = ctx->aux_host[m];
+            A.wsum = (float)B.wsum[l];
+            A.ubx_rel = (float)(B.Ubx[l] - ctx->cfg.u_in * B.wsum[l]);
+            A.uby_rel = (float)B.Uby[l];
+            A.body = b;
+        }
+    }
+    std::sort(ents.begin(), ents.end(), [](const Ent& a, const Ent& b) {
+        return a.node != b.node ? a.node < b.node : a.marker < b.marker;
+    });
+    // Band segments: 128-node runs of a row holding at least one band node.
+    std::vector<int> seg_index((size_t)ny * ctx->nseg, -1);
+    std::vector<long long> seg_keys;
+    for (const Ent& e : ents) {
+        const long long y = e.node / nx, x = e.node % nx;
+        const long long key = y * ctx->nseg + x / kSeg;
+        if (seg_keys.empty() || seg_keys.back() != key) seg_keys.push_back(key);
+    }
+    ctx->nband = (int)seg_keys.size();
+    for (int s = 0; s < ctx->nband; s++) seg_index[seg_keys[s]] = s;
+    std::vector<int> seg_ptr((size_t)ctx->nband * (kSeg + 1), 0);
+    std::vector<CsrEntry> csr(ents.size());
+    {
+        // entries are sorted by node, so each segment's entries are contiguous
+        size_t k = 0;
+        for (int s = 0; s < ctx->nband; s++) {
+            const long long key = seg_keys[s];
+            const long long y = key / ctx->nseg, xs0 = (key % ctx->nseg) * kSeg;
+            int* ptr = &seg_ptr[(size_t)s * (kSeg + 1)];
+            for (int i = 0; i < kSeg; i++) {
+                ptr[i] = (int)k;
+                const long long node = y * nx + xs0 + i;
+                while (k < ents.size() && ents[k].node == node && xs0 + i < nx) {
+                    csr[k].marker = ents[k].marker;
+                    csr[k].w = (float)ents[k].w;
+                    k++;
+                }
+            }
+            ptr[kSeg] = (int)k;
+        }
+    }
+    const size_t nseg_all = (size_t)ny * ctx->nseg;
+    const size_t bytes_before = ctx->dev_bytes;
+    CK(dalloc(ctx, &ctx->d_mk, sizeof(Marker) * nm));
+    CK(dalloc(ctx, &ctx->d_aux, sizeof(MarkerAux) * nm));
+    CK(dalloc(ctx, &ctx->d_F[0], sizeof(float2) * nm));
+    CK(dalloc(ctx, &ctx->d_F[1], sizeof(float2) * nm));
+    CK(dalloc(ctx, &ctx->d_Us, sizeof(float2) * nm));
+    CK(dalloc(ctx, &ctx->d_rhol, sizeof(float) * nm));
+    CK(dalloc(ctx, &ctx->d_seg_index, sizeof(int) * nseg_all));
+    CK(dalloc(ctx, &ctx->d_seg_ptr, sizeof(int) * std::max<size_t>(seg_ptr.size(), 1)));
+    CK(dalloc(ctx, &ctx->d_csr, sizeof(CsrEntry) * std::max<size_t>(csr.size(), 1)));
+    CK(dalloc(ctx, &ctx->d_body_ptr, sizeof(int) * (nb + 1)));
+    CK(dalloc(ctx, &ctx->d_body_scale, sizeof(double) * nb));
+    CK(dalloc(ctx, &ctx->d_hist, sizeof(double2) * (size_t)ctx->cfg.history_len * nb));
+    cudaStream_t st = ctx->stream;
+    CK(cudaMemcpyAsync(ctx->d_mk, mk.data(), sizeof(Marker) * nm, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ctx->d_aux, ctx->aux_host.data(), sizeof(MarkerAux) * nm,
+                       cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(ctx->d_F[0], 0, sizeof(float2) * nm, st));
+    CK(cudaMemsetAsync(ctx->d_F[1], 0, sizeof(float2) * nm, st));
+    CK(cudaMemsetAsync(ctx->d_Us, 0, sizeof(float2) * nm, st));
+    CK(cudaMemsetAsync(ctx->d_rhol, 0, sizeof(float) * nm, st));
+    CK(cudaMemcpyAsync(ctx->d_seg_index, seg_index.data(), sizeof(int) * nseg_all,
+                       cudaMemcpyHostToDevice, st));
+    if (!seg_ptr.empty())
+        CK(cudaMemcpyAsync(ctx->d_seg_ptr, seg_ptr.data(), sizeof(int) * seg_ptr.size(),
+                           cudaMemcpyHostToDevice, st));
+    if (!csr.empty())
+        CK(cudaMemcpyAsync(ctx->d_csr, csr.data(), sizeof(CsrEntry) * csr.size(),
+                           cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ctx->d_body_ptr, body_ptr.data(), sizeof(int) * (nb + 1),
+                       cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ctx->d_body_scale, scale.data(), sizeof(double) * nb,
+                       cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(ctx->d_hist, 0, sizeof(double2) * (size_t)ctx->cfg.history_len * nb, st));
+    CK(cudaStreamSynchronize(st));
+    ctx->marker_bytes = ctx->dev_bytes - bytes_before;
+    ctx->hist_from = ctx->steps;
+    return BTDF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int btdf_version(void) { return 1; }
+
+const char* btdf_status_string(int s) {
+    switch (s) {
+    case BTDF_OK: return "ok";
+    case BTDF_EINVAL: return "invalid argument";
+    case BTDF_ENOMEM: return "out of memory";
+    case BTDF_ECUDA: return "CUDA error";
+    case BTDF_EUNSTABLE: return "unstable (density or force at a marker)";
+    case BTDF_ETIMEOUT: return "device wait timed out";
+    case BTDF_ESTATE: return "invalid state for this call";
+    default: return "unknown status";
+    }
+}
+
+const char* btdf_last_error(const btdf_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int btdf_config_default(btdf_config* cfg) {
+    if (!cfg) return BTDF_EINVAL;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->nx = 64;
+    cfg->ny = 64;
+    cfg->tau = 0.6;
+    cfg->u_in = 0.0;
+    cfg->delta = BTDF_DELTA3;
+    cfg->nf = 1;
+    cfg->storage = BTDF_F32;
+    cfg->bc_x = BTDF_BCX_PERIODIC;
+    cfg->bc_y = BTDF_BCY_PERIODIC;
+    cfg->history_len = 4096;
+    return BTDF_OK;
+}
+
+int btdf_create(const btdf_config* cfg, void* stream, btdf_ctx** out) {
+    if (!cfg || !out) return BTDF_EINVAL;
+    *out = nullptr;
+    const btdf_config& c = *cfg;
+    if (c.nx < 4 || c.ny < 4 || (long long)c.nx * c.ny > (1ll << 31)) return BTDF_EINVAL;
+    if (!(c.tau > 0.5) || !std::isfinite(c.tau)) return BTDF_EINVAL;
+    if (support_width(c.delta) == 0) return BTDF_EINVAL;
+    if (c.nf < 1 || c.nf > 64) return BTDF_EINVAL;
+    if (c.storage < 0 || c.storage > 2) return BTDF_EINVAL;
+    if (c.bc_x < 0 || c.bc_x > 1 || c.bc_y < 0 || c.bc_y > 2) return BTDF_EINVAL;
+    if (c.history_len < 1) return BTDF_EINVAL;
+    if (!std::isfinite(c.u_in) || std::fabs(c.u_in) >= 0.5) return BTDF_EINVAL;
+    if (!std::isfinite(c.gx) || !std::isfinite(c.gy)) return BTDF_EINVAL;
+
+    btdf_ctx* ctx = new (std::nothrow) btdf_ctx();
+    if (!ctx) return BTDF_ENOMEM;
+    ctx->cfg = c;
+    ctx->stream = (cudaStream_t)stream;
+    ctx->width = support_width(c.delta);
+    ctx->nxp = (c.nx + 31) / 32 * 32;
+    ctx->nseg = (ctx->nxp + kSeg - 1) / kSeg;
+    ctx->plane = (long long)ctx->nxp * c.ny;
+    ctx->elem = elem_bytes(c.storage);
+    auto bail = [&](int code) {
+        btdf_destroy(ctx);
+        return code;
+    };
+    cudaError_t e = cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(BTDF_ECUDA);
+    const size_t bytes = (size_t)9 * ctx->plane * ctx->elem;
+    for (int i = 0; i < 2; i++) {
+        e = dalloc(ctx, &ctx->g[i], bytes);
+        if (e == cudaErrorMemoryAllocation) return bail(BTDF_ENOMEM);
+        if (e != cudaSuccess) return bail(BTDF_ECUDA);
+        if (cudaMemsetAsync(ctx->g[i], 0, bytes, ctx->stream) != cudaSuccess) return bail(BTDF_ECUDA);
+    }
+    if (dalloc(ctx, &ctx->d_step, sizeof(unsigned long long)) != cudaSuccess ||
+        dalloc(ctx, &ctx->d_ticket, sizeof(unsigned int)) != cudaSuccess ||
+        dalloc(ctx, &ctx->d_status, sizeof(int)) != cudaSuccess)
+        return bail(BTDF_ECUDA);
+    if (cudaMemsetAsync(ctx->d_step, 0, sizeof(unsigned long long), ctx->stream) != cudaSuccess ||
+        cudaMemsetAsync(ctx->d_ticket, 0, sizeof(unsigned int), ctx->stream) != cudaSuccess ||
+        cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream) != cudaSuccess ||
+        cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+        return bail(BTDF_ECUDA);
+    *out = ctx;
+    return BTDF_OK;
+}
+
+int btdf_destroy(btdf_ctx* ctx) {
+    if (!ctx) return BTDF_EINVAL;
+    if (ctx->stream || ctx->g[0]) cudaStreamSynchronize(ctx->stream);
+    drop_graphs(ctx);
+    free_markers(ctx);
+    dfree(ctx, ctx->g[0]);
+    dfree(ctx, ctx->g[1]);
+    dfree(ctx, ctx->d_step);
+    dfree(ctx, ctx->d_ticket);
+    dfree(ctx, ctx->d_status);
+    for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+    if (ctx->cap) cudaStreamDestroy(ctx->cap);
+    delete ctx;
+    return BTDF_OK;
+}
+
+int btdf_init_fields(btdf_ctx* ctx, const double* rho, const double* ux, const double* uy) {
+    if (!ctx || !rho || !ux || !uy) return fail(ctx, BTDF_EINVAL, "null argument");
+    const size_t nn = (size_t)ctx->cfg.nx * ctx->cfg.ny;
+    for (size_t i = 0; i < nn; i++)
+        if (!(rho[i] > 0.0) || !std::isfinite(rho[i]) || !std::isfinite(ux[i]) || !std::isfinite(uy[i]))
+            return fail(ctx, BTDF_EINVAL, "initial fields must be finite with rho > 0");
+    double* d = nullptr;
+    CK(cudaMalloc((void**)&d, sizeof(double) * 3 * nn));
+    cudaStream_t st = ctx->stream;
+    int rc = BTDF_OK;
+    auto run = [&]() -> int {
+        CK(cudaMemcpyAsync(d, rho, sizeof(double) * nn, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(d + nn, ux, sizeof(double) * nn, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(d + 2 * nn, uy, sizeof(double) * nn, cudaMemcpyHostToDevice, st));
+        const size_t bytes = (size_t)9 * ctx->plane * ctx->elem;
+        CK(cudaMemsetAsync(ctx->g[0], 0, bytes, st));
+        CK(cudaMemsetAsync(ctx->g[1], 0, bytes, st));
+        const LatticeParams p = lattice_params(ctx);
+        CK(launch_init_equilibrium(ctx->cfg.storage, ctx->g[0], p, d, d + nn, d + 2 * nn, st));
+        CK(cudaMemsetAsync(ctx->d_step, 0, sizeof(unsigned long long), st));
+        CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
+        CK(cudaStreamSynchronize(st));
+        return BTDF_OK;
+    };
+    rc = run();
+    cudaFree(d);
+    if (rc != BTDF_OK) return rc;
+    ctx->cur = 0;
+    ctx->poststream = true;
+    ctx->has_fields = true;
+    ctx->steps = 0;
+    ctx->hist_from = 0;
+    return BTDF_OK;
+}
+
+int btdf_add_markers(btdf_ctx* ctx, int32_t n, const double* X, const double* Y, const double* Ubx,
+                     const double* Uby, double ds, double drs, int32_t* body_id) {
+    if (!ctx) return BTDF_EINVAL;
+    if (n < 1 || !X || !Y || !(ds > 0.0) || !std::isfinite(ds) || !std::isfinite(drs))
+        return fail(ctx, BTDF_EINVAL, "need n >= 1 markers, positions and ds > 0");
+    if ((long long)ctx->nmark + n > (1ll << 30)) return fail(ctx, BTDF_EINVAL, "too many markers");
+    const int nx = ctx->cfg.nx, ny = ctx->cfg.ny;
+    const double half = 0.5 * ctx->width;
+    for (int l = 0; l < n; l++) {
+        if (!std::isfinite(X[l]) || !std::isfinite(Y[l]))
+            return fail(ctx, BTDF_EINVAL, "marker position not finite");
+        if ((Ubx && !std::isfinite(Ubx[l])) || (Uby && !std::isfinite(Uby[l])))
+            return fail(ctx, BTDF_EINVAL, "marker velocity not finite");
+        const bool inx = ctx->cfg.bc_x == kBcxPeriodic || (X[l] > -half && X[l] < nx - 1 + half);
+        const bool iny = ctx->cfg.bc_y == kBcyPeriodic || (Y[l] > -half && Y[l] < ny - 1 + half);
+        if (!inx || !iny) return fail(ctx, BTDF_EINVAL, "marker support lies outside the lattice");
+        if ((ctx->cfg.bc_x == kBcxPeriodic && std::fabs(X[l]) > 1e9) ||
+            (ctx->cfg.bc_y == kBcyPeriodic && std::fabs(Y[l]) > 1e9))
+            return fail(ctx, BTDF_EINVAL, "marker position out of range");
+    }
+    Body B;
+    B.first = ctx->nmark;
+    B.n = n;
+    B.ds = ds;
+    B.drs = drs > 0.0 ? drs : paper_drs(ctx->cfg.delta);
+    B.X.assign(X, X + n);
+    B.Y.assign(Y, Y + n);
+    B.Ubx.assign(n, 0.0);
+    B.Uby.assign(n, 0.0);
+    if (Ubx) B.Ubx.assign(Ubx, Ubx + n);
+    if (Uby) B.Uby.assign(Uby, Uby + n);
+    const int id = (int)ctx->bodies.size();
+    ctx->bodies.push_back(std::move(B));
+    ctx->nmark += n;
+    const int rc = rebuild_markers(ctx);
+    if (rc != BTDF_OK) return rc;
+    if (body_id) *body_id = id;
+    return BTDF_OK;
+}
+
+int btdf_set_marker_velocity(btdf_ctx* ctx, int32_t body, const double* Ubx, const double* Uby) {
+    if (!ctx) return BTDF_EINVAL;
+    if (body < 0 || body >= (int)ctx->bodies.size() || !Ubx || !Uby)
+        return fail(ctx, BTDF_EINVAL, "bad body index or null velocity");
+    Body& B = ctx->bodies[body];
+    for (int l = 0; l < B.n; l++)
+        if (!std::isfinite(Ubx[l]) || !std::isfinite(Uby[l]))
+            return fail(ctx, BTDF_EINVAL, "marker velocity not finite");
+    for (int l = 0; l < B.n; l++) {
+        B.Ubx[l] = Ubx[l];
+        B.Uby[l] = Uby[l];
+        MarkerAux& A = ctx->aux_host[B.first + l];
+        A.ubx_rel = (float)(Ubx[l] - ctx->cfg.u_in * B.wsum[l]);
+        A.uby_rel = (float)Uby[l];
+    }
+    CK(cudaMemcpyAsync(ctx->d_aux + B.first, ctx->aux_host.data() + B.first, sizeof(MarkerAux) * B.n,
+                       cudaMemcpyHostToDevice, ctx->stream));
+    // the host copy may change again before the copy runs: make it complete
+    CK(cudaStreamSynchronize(ctx->stream));
+    return BTDF_OK;
+}
+
+int btdf_step(btdf_ctx* ctx, int64_t nsteps) {
+    if (!ctx) return BTDF_EINVAL;
+    if (nsteps < 0) return fail(ctx, BTDF_EINVAL, "nsteps < 0");
+    if (!ctx->has_fields) return fail(ctx, BTDF_ESTATE, "call btdf_init_fields or btdf_load_state first");
+    int64_t i = 0;
+    if (nsteps > 0 && ctx->poststream) {
+        const int rc = enqueue_step(ctx, ctx->stream, false, ctx->cur, ctx->prof);
+        if (rc != BTDF_OK) return rc;
+        ctx->cur = 1 - ctx->cur;
+        ctx->poststream = false;
+        i = 1;
+    }
+    if (!ctx->prof) {
+        while (nsteps - i >= kGraphSteps) {
+            const int rc = ensure_graph(ctx, ctx->cur);
+            if (rc != BTDF_OK) return rc;
+            CK(cudaGraphLaunch(ctx->gexec[ctx->cur], ctx->stream));
+            i += kGraphSteps;
+        }
+    }
+    for (; i < nsteps; i++) {
+        const int rc = enqueue_step(ctx, ctx->stream, true, ctx->cur, ctx->prof);
+        if (rc != BTDF_OK) return rc;
+        ctx->cur = 1 - ctx->cur;
+    }
+    ctx->steps += nsteps;
+    return BTDF_OK;
+}
+
+int btdf_sync(btdf_ctx* ctx) {
+    if (!ctx) return BTDF_EINVAL;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return read_status(ctx);
+}
+
+int64_t btdf_step_count(const btdf_ctx* ctx) { return ctx ? ctx->steps : -1; }
+
+int btdf_read_forces(btdf_ctx* ctx, int32_t body, int64_t first, int64_t n, double* Fx, double* Fy) {
+    if (!ctx) return BTDF_EINVAL;
+    if (body < 0 || body >= (int)ctx->bodies.size() || n < 0 || (n > 0 && (!Fx || !Fy)))
+        return fail(ctx, BTDF_EINVAL, "bad body index, count or null output");
+    const int64_t H = ctx->cfg.history_len;
+    if (first < ctx->hist_from || first < ctx->steps - H || first + n > ctx->steps)
+        return fail(ctx, BTDF_EINVAL, "requested steps are not in the force history");
+    const int nb = (int)ctx->bodies.size();
+    std::vector<double2> tmp((size_t)n);
+    int64_t done = 0;
+    while (done < n) {
+        const int64_t s = first + done;
+        const int64_t slot = s % H;
+        const int64_t cnt = std::min<int64_t>(n - done, H - slot);
+        CK(cudaMemcpy2DAsync(tmp.data() + done, sizeof(double2), ctx->d_hist + slot * nb + body,
+                             sizeof(double2) * nb, sizeof(double2), (size_t)cnt,
+                             cudaMemcpyDeviceToHost, ctx->stream));
+        done += cnt;
+    }
+    const int rc = read_status(ctx);
+    for (int64_t i = 0; i < n; i++) {
+        Fx[i] = tmp[i].x;
+        Fy[i] = tmp[i].y;
+    }
+    return rc;
+}
+
+int btdf_read_markers(btdf_ctx* ctx, int32_t body, float* Usx, float* Usy, float* Fbx, float* Fby) {
+    if (!ctx) return BTDF_EINVAL;
+    if (body < 0 || body >= (int)ctx->bodies.size()) return fail(ctx, BTDF_EINVAL, "bad body index");
+    const Body& B = ctx->bodies[body];
+    std::vector<float2> us(B.n), F(B.n);
+    CK(cudaMemcpyAsync(us.data(), ctx->d_Us + B.first, sizeof(float2) * B.n, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaMemcpyAsync(F.data(), ctx->d_F[(ctx->cfg.nf - 1) % 2] + B.first, sizeof(float2) * B.n,
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    const int rc = read_status(ctx);
+    for (int l = 0; l < B.n; l++) {
+        if (Usx) Usx[l] = us[l].x;
+        if (Usy) Usy[l] = us[l].y;
+        if (Fbx) Fbx[l] = F[l].x;
+        if (Fby) Fby[l] = F[l].y;
+    }
+    return rc;
+}
+
+int btdf_read_field(btdf_ctx* ctx, int32_t kind, float* dst, int32_t dst_is_device) {
+    if (!ctx) return BTDF_EINVAL;
+    if (kind < 0 || kind > 3 || !dst) return fail(ctx, BTDF_EINVAL, "bad field kind or null output");
+    if (!ctx->has_fields) return fail(ctx, BTDF_ESTATE, "no fields");
+    const size_t nn = (size_t)ctx->cfg.nx * ctx->cfg.ny * (kind == 3 ? 9 : 1);
+    float* d = dst;
+    if (!dst_is_device) CK(cudaMalloc((void**)&d, sizeof(float) * nn));
+    int rc = BTDF_OK;
+    auto run = [&]() -> int {
+        const LatticeParams p = lattice_params(ctx);
+        CK(launch_read_field(ctx->cfg.storage, !ctx->poststream, ctx->g[ctx->cur], p, kind, d,
+                             ctx->stream));
+        if (!dst_is_device)
+            CK(cudaMemcpyAsync(dst, d, sizeof(float) * nn, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        return BTDF_OK;
+    };
+    rc = run();
+    if (!dst_is_device) cudaFree(d);
+    if (rc != BTDF_OK) return rc;
+    return read_status(ctx);
+}
+
+int btdf_state_size(btdf_ctx* ctx, size_t* bytes) {
+    if (!ctx || !bytes) return BTDF_EINVAL;
+    *bytes = sizeof(StateHeader) + (size_t)9 * ctx->plane * ctx->elem;
+    return BTDF_OK;
+}
+
+int btdf_save_state(btdf_ctx* ctx, void* dst, size_t cap, size_t* used) {
+    if (!ctx || !dst) return BTDF_EINVAL;
+    if (!ctx->has_fields) return fail(ctx, BTDF_ESTATE, "no fields");
+    size_t need = 0;
+    btdf_state_size(ctx, &need);
+    if (cap < need) return fail(ctx, BTDF_EINVAL, "destination buffer too small");
+    StateHeader h{kStateMagic, ctx->cfg.nx, ctx->cfg.ny, ctx->nxp, ctx->cfg.storage,
+                  ctx->poststream ? 1 : 0, 0, ctx->steps};
+    std::memcpy(dst, &h, sizeof(h));
+    CK(cudaMemcpyAsync((char*)dst + sizeof(h), ctx->g[ctx->cur], need - sizeof(h),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (used) *used = need;
+    return read_status(ctx);
+}
+
+int btdf_load_state(btdf_ctx* ctx, const void* src, size_t len) {
+    if (!ctx || !src) return BTDF_EINVAL;
+    size_t need = 0;
+    btdf_state_size(ctx, &need);
+    if (len < need) return fail(ctx, BTDF_EINVAL, "checkpoint too short");
+    StateHeader h;
+    std::memcpy(&h, src, sizeof(h));
+    if (h.magic != kStateMagic || h.nx != ctx->cfg.nx || h.ny != ctx->cfg.ny || h.nxp != ctx->nxp ||
+        h.storage != ctx->cfg.storage || h.steps < 0)
+        return fail(ctx, BTDF_EINVAL, "checkpoint does not match this context");
+    CK(cudaMemcpyAsync(ctx->g[ctx->cur], (const char*)src + sizeof(h), need - sizeof(h),
+                       cudaMemcpyHostToDevice, ctx->stream));
+    unsigned long long s = (unsigned long long)h.steps;
+    CK(cudaMemcpyAsync(ctx->d_step, &s, sizeof(s), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->poststream = h.poststream != 0;
+    ctx->has_fields = true;
+    ctx->steps = h.steps;
+    ctx->hist_from = h.steps;
+    return BTDF_OK;
+}
+
+int btdf_profile_enable(btdf_ctx* ctx, int32_t on) {
+    if (!ctx) return BTDF_EINVAL;
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->prof = on != 0;
+    ctx->ev_used = 0;
+    return BTDF_OK;
+}
+
+int btdf_profile_read(btdf_ctx* ctx, double* ms_ib, double* ms_lbm, int64_t* launches_ib,
+                      int64_t* launches_lbm) {
+    if (!ctx) return BTDF_EINVAL;
+    CK(cudaStreamSynchronize(ctx->stream));
+    double a = 0.0, b = 0.0;
+    const int64_t nst = (int64_t)(ctx->ev_used / 3);
+    for (int64_t i = 0; i < nst; i++) {
+        float t1 = 0.f, t2 = 0.f;
+        CK(cudaEventElapsedTime(&t1, ctx->ev[3 * i], ctx->ev[3 * i + 1]));
+        CK(cudaEventElapsedTime(&t2, ctx->ev[3 * i + 1], ctx->ev[3 * i + 2]));
+        a += t1;
+        b += t2;
+    }
+    if (ms_ib) *ms_ib = a;
+    if (ms_lbm) *ms_lbm = b;
+    if (launches_ib) *launches_ib = ctx->nmark > 0 ? nst * ctx->cfg.nf : 0;
+    if (launches_lbm) *launches_lbm = nst;
+    return BTDF_OK;
+}
+
+int btdf_device_bytes(const btdf_ctx* ctx, size_t* bytes) {
+    if (!ctx || !bytes) return BTDF_EINVAL;
+    *bytes = ctx->dev_bytes;
+    return BTDF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,119 @@
+// btdf_internal.cuh - structures shared by the host side and the kernels of
+// the BTDF-IB/LBM library (not part of the public C ABI).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+
+namespace btdf {
+
+// One warp owns a run of kSeg consecutive nodes of one lattice row: 32 lanes
+// x 4 nodes, so every population plane is read and written with 16-byte
+// (FP32) or 8-byte (FP16/BF16) vectors.
+constexpr int kSeg = 128;
+constexpr int kNodesPerLane = 4;
+constexpr int kThreads = 256;
+
+// D2Q9 velocities and weights (Eq. 8 and the weights stated below Eq. 7).
+__host__ __device__ constexpr int ex(int a) {
+    return (a == 1 || a == 5 || a == 8) ? 1 : ((a == 3 || a == 6 || a == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int ey(int a) {
+    return (a == 2 || a == 5 || a == 6) ? 1 : ((a == 4 || a == 7 || a == 8) ? -1 : 0);
+}
+__host__ __device__ constexpr float wt(int a) {
+    return a == 0 ? 4.0f / 9.0f : (a < 5 ? 1.0f / 9.0f : 1.0f / 36.0f);
+}
+// Population with the normal (y) component reversed: specular reflection.
+__host__ __device__ constexpr int mirror_y(int a) {
+    return a == 2 ? 4 : a == 4 ? 2 : a == 5 ? 8 : a == 8 ? 5 : a == 6 ? 7 : a == 7 ? 6 : a;
+}
+// Population with both components reversed: bounce-back.
+__host__ __device__ constexpr int opposite(int a) {
+    return a == 0 ? 0 : (a <= 4 ? ((a + 1) % 4) + 1 : ((a - 3) % 4) + 5);
+}
+
+enum : int { kBcxPeriodic = 0, kBcxInout = 1 };
+enum : int { kBcyPeriodic = 0, kBcyFreeslip = 1, kBcyNoslip = 2 };
+enum : int { kStoreF32 = 0, kStoreF16 = 1, kStoreBF16 = 2 };
+
+// Static per-marker data evaluated once on the host in FP64 (Eq. 14):
+// support node coordinates (wrapped on periodic axes, clamped and given zero
+// weight where a bounded axis cuts the support) and the 2-D weights
+// w[j*S + i] = delta(x_i - X) delta(y_j - Y).
+struct Marker {
+    int xs[4];
+    int ys[4];
+    float w[16];
+};
+
+// Per-marker values the IB kernel needs besides the weights.  Velocities are
+// stored relative to the reference velocity U_r (see LatticeParams):
+// ub_rel = U_b - U_r * wsum, with wsum = sum of the marker's weights (1 unless
+// a bounded lattice edge clips the support), both evaluated in FP64.
+struct MarkerAux {
+    float ubx_rel, uby_rel;
+    float wsum;
+    int body;
+};
+
+// One term of the node-centric spread (Eq. 15): the marker and its
+// pre-multiplied weight delta*delta*drs*ds (dh = 1).
+struct CsrEntry {
+    int marker;
+    float w;
+};
+
+struct LatticeParams {
+    int nx, ny, nxp, nseg;
+    long long plane;           // elements per population plane (nxp * ny)
+    int bcx, bcy;
+    float omega;               // 1 / tau
+    float guo;                 // 1 - 1 / (2 tau)
+    float u_in;
+    // Reference velocity U_r = (urx, ury): the buffers store
+    // d_a = f_a - f_eq_a(1, U_r), so FP32 rounding scales with the departure
+    // of the flow from the free stream rather than with the flow itself.
+    float urx, ury;
+    float gx, gy;              // uniform body force
+    const int* seg_index;      // [ny * nseg] band segment id or -1 (null: no band)
+    const int* seg_ptr;        // [nband * (kSeg + 1)] CSR row pointers per node
+    const CsrEntry* csr;
+    const float2* F;           // Lagrangian forces of the step (sum of passes)
+    unsigned long long* step;  // device step counter, advanced by the LBM kernel
+};
+
+struct IbParams {
+    int nmark, nbody;
+    const Marker* mk;
+    const MarkerAux* aux;
+    const float2* F_prev;      // forces accumulated by earlier passes (null on pass 1)
+    float2* F_out;             // F_prev + this pass's increment
+    float2* Us;                // D_I u* of pass 1 (diagnostic)
+    float* rhol;               // D_I rho (diagnostic)
+    int first_pass, last_pass;
+    const int* body_ptr;       // [nbody + 1] marker ranges
+    const double* body_scale;  // ds * drs per body
+    double2* hist;             // [hist_len * nbody] force on each body per step
+    int hist_len;
+    const unsigned long long* step;
+    unsigned int* ticket;      // last-block-done counter, returned to 0 by that block
+    int* status;               // sticky device status bits
+};
+
+enum : int { kStatusUnstable = 1, kStatusTimeout = 2 };
+
+// Launchers implemented in btdf_kernels.cu.
+cudaError_t launch_collide_stream(int storage, bool pull, const void* gin, void* gout,
+                                  const LatticeParams& p, cudaStream_t st);
+cudaError_t launch_ib_force(int storage, bool pull, int width, const void* g,
+                            const LatticeParams& p, const IbParams& q, cudaStream_t st);
+cudaError_t launch_init_equilibrium(int storage, void* g, const LatticeParams& p,
+                                    const double* rho, const double* ux, const double* uy,
+                                    cudaStream_t st);
+cudaError_t launch_read_field(int storage, bool pull, const void* g, const LatticeParams& p,
+                              int kind, float* dst, cudaStream_t st);
+
+}  // namespace btdf

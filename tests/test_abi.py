@@ -1,0 +1,73 @@
+"""The C-ABI library loads, exports every symbol include/btdf.h declares, and
+rejects invalid configurations on the host before touching the GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1806_09403_gb300 import _build
+from paper_1806_09403_gb300 import btdf as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    _build.build()
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "btdf.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(btdf_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported():
+    L = ctypes.CDLL(_build.LIB)
+    decl = declared_symbols()
+    assert len(decl) >= 20
+    for name in decl:
+        assert hasattr(L, name), name
+    assert sorted(B.EXPORTS) == decl
+
+
+def test_config_struct_size_matches():
+    # 2 int32 + 2 double + 6 int32 + 2 double, no padding holes
+    assert ctypes.sizeof(B.btdf_config) == 64
+
+
+def test_version_and_status_strings():
+    assert B.btdf_version() >= 1
+    for rc in (0, -1, -2, -3, -4, -5, -6):
+        assert B.btdf_status_string(rc) != "unknown status"
+
+
+@pytest.mark.parametrize("field,value", [
+    ("tau", 0.5), ("tau", float("nan")), ("nx", 3), ("ny", 0), ("delta", 1), ("delta", 6),
+    ("nf", 0), ("nf", 65), ("storage", 3), ("bc_x", 2), ("bc_y", 3), ("history_len", 0),
+    ("u_in", float("inf")), ("u_in", 0.6), ("gx", float("nan")),
+])
+def test_invalid_config_rejected_on_host(field, value):
+    cfg = B.btdf_config_default()
+    setattr(cfg, field, value)
+    rc, ctx = B.btdf_create(cfg)
+    assert rc == B.BTDF_EINVAL
+    assert not ctx
+
+
+def test_null_arguments_rejected():
+    L = B.lib()
+    assert L.btdf_create(None, None, None) == B.BTDF_EINVAL
+    assert L.btdf_destroy(None) == B.BTDF_EINVAL
+    assert L.btdf_step(None, 1) == B.BTDF_EINVAL
+    assert L.btdf_step_count(None) == -1
+
+
+def test_no_gpu_reports_cuda_error_not_fallback():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    cfg = B.btdf_config_default()
+    rc, ctx = B.btdf_create(cfg)
+    assert rc == B.BTDF_ECUDA and not ctx

@@ -1,0 +1,317 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Both sides get the same seeded inputs from ``workloads``.  Tolerances (FP32
+arithmetic against FP64):
+  * velocity field after the run: relative L2 over all nodes (Eq. 43) <= 1e-5;
+  * drag: |Cd_gpu - Cd_ref| <= 1e-4 * max(|Cd_ref(t)|, Cd_scale) at every step,
+    Cd_scale = mean |Cd_ref| over the run (the relative error is ill-posed where
+    the early transient crosses zero);
+  * lift: |Cl_gpu - Cl_ref| <= 1e-4 * max(|Cl_ref(t)|, |Cd_ref(t)|, Cd_scale).
+The 1e-5 / 1e-4 bars apply to the cylinder cases of the paper over 1000 steps.
+Other cases (Taylor-Green, Poiseuille, tiny lattices) run flows that change
+slowly from step to step; there the FP32 rounding of a stored population
+repeats almost unchanged every step and accumulates coherently, so after n
+steps the velocity error is bounded by about n * 2^-24 relative.  Those tests
+use tol(n) = max(1e-5, n * 2^-24).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1806_09403_gb300 import _build  # noqa: E402
+from paper_1806_09403_gb300 import btdf as B  # noqa: E402
+
+VEL_TOL = 1e-5
+CD_TOL = 1e-4
+
+
+def coherent_tol(n):
+    return max(VEL_TOL, n * 2.0 ** -24)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    _build.build()
+    O.set_threads(min(os.cpu_count() or 1, 32))
+
+
+def rel_l2(ux, uy, rx, ry):
+    num = ((ux - rx) ** 2 + (uy - ry) ** 2).sum()
+    den = (rx ** 2 + ry ** 2).sum()
+    return float(np.sqrt(num / den))
+
+
+def run_both(case, steps, storage=B.BTDF_F32, chunks=None):
+    lat = B.Lattice.from_case(case, storage=storage, history_len=max(steps, 1))
+    sim = O.Sim.from_case(case)
+    for n in (chunks or [steps]):
+        lat.step(n)
+        sim.step(n)
+    lat.sync()
+    return lat, sim
+
+
+def check_fields(lat, sim, tol=VEL_TOL):
+    r, ux, uy = lat.moments()
+    R, UX, UY = sim.moments()
+    e = rel_l2(ux.astype(np.float64), uy.astype(np.float64), UX, UY)
+    er = float(np.abs(r - R).max())
+    assert np.isfinite(ux).all() and np.isfinite(uy).all()
+    assert e <= tol, f"velocity rel L2 {e:.3e} > {tol:.1e}"
+    assert er <= 1e-5, f"density max err {er:.3e}"
+    return e
+
+
+def check_forces(lat, sim, case, body=0, tol=CD_TOL):
+    steps = sim.steps
+    gx, gy = lat.forces(body, 0, steps)
+    rx, ry = sim.history(body, 0, steps)
+    q = 0.5 * case.u_in ** 2 * (case.D if case.D > 0 else 1.0)
+    cd, cl, CD, CL = gx / q, gy / q, rx / q, ry / q
+    scale = np.abs(CD).mean()
+    ecd = np.abs(cd - CD) / np.maximum(np.abs(CD), scale)
+    ecl = np.abs(cl - CL) / np.maximum(np.maximum(np.abs(CL), np.abs(CD)), scale)
+    assert ecd.max() <= tol, f"Cd err {ecd.max():.3e} at step {ecd.argmax()}"
+    assert ecl.max() <= tol, f"Cl err {ecl.max():.3e} at step {ecl.argmax()}"
+    return float(ecd.max()), float(ecl.max())
+
+
+@pytest.mark.parametrize("delta", [4, 5])
+def test_small_cylinder_1000_steps(delta):
+    """160 x 80 lattice, D = 16, 50 markers, Re = 40, 1000 steps."""
+    case = W.small_cylinder(delta=delta)
+    lat, sim = run_both(case, 1000, chunks=[1, 63, 64, 872])
+    e = check_fields(lat, sim)
+    ecd, ecl = check_forces(lat, sim, case)
+    # per-marker results of the last step
+    # F_b = 2 rho (U_b - U*) inherits U*'s absolute error: 2 * 1e-5 * U = 1e-6
+    m = lat.markers(0)
+    d = sim.marker_diag(0)
+    assert np.abs(m["Usx"] - d["Usx"]).max() <= 1e-5 * case.u_in
+    assert np.abs(m["Fbx"] - d["Fbx"]).max() <= 2e-5 * case.u_in
+    assert np.abs(m["Fby"] - d["Fby"]).max() <= 2e-5 * case.u_in
+
+
+@pytest.mark.parametrize("delta", [2, 3, 4, 5])
+def test_delta_kinds(delta):
+    case = W.small_cylinder(delta=delta, seed=11)
+    case.nx, case.ny = 96, 48
+    case.bodies = [W.circle_markers(30.3, 23.6, 12.0, 38)]
+    case.D = 12.0
+    lat, sim = run_both(case, 300)
+    check_fields(lat, sim)
+    check_forces(lat, sim, case)
+
+
+@pytest.mark.parametrize("re,delta", [(0.1, 3), (40.0, 2), (200.0, 4)])
+def test_paper_cylinder_first_steps(re, delta):
+    """1600 x 800, D = 40, 126 markers: the full-size lattice, first 100 steps."""
+    case = W.paper_cylinder(re=re, delta=delta)
+    lat, sim = run_both(case, 100)
+    check_fields(lat, sim)
+    check_forces(lat, sim, case)
+
+
+@pytest.mark.slow
+def test_paper_cylinder_1000_steps():
+    """The benchmarked configuration (Re = 200, 3-point delta) over 1000 steps."""
+    case = W.paper_cylinder(re=200.0, delta=3)
+    lat, sim = run_both(case, 1000)
+    check_fields(lat, sim)
+    check_forces(lat, sim, case)
+
+
+def test_taylor_green_periodic():
+    n = 64
+    rho, ux, uy = W.taylor_green_fields(n, 0.02)
+    lat = B.Lattice(n, n, 0.65)
+    sim = O.Sim(n, n, 0.65)
+    lat.init_fields(rho, ux, uy)
+    sim.init_fields(rho, ux, uy)
+    lat.step(500)
+    sim.step(500)
+    check_fields(lat, sim, tol=coherent_tol(500))
+
+
+def test_poiseuille_noslip_with_body_force():
+    lat = B.Lattice(8, 32, 0.9, bc_x=B.BTDF_BCX_PERIODIC, bc_y=B.BTDF_BCY_NOSLIP, gx=1e-5)
+    sim = O.Sim(8, 32, 0.9, 0.0, 0, 2, 1e-5, 0.0, 3, 1)
+    z = np.zeros((32, 8))
+    lat.init_fields(z + 1, z, z)
+    sim.init_fields(z + 1, z, z)
+    lat.step(3000)
+    sim.step(3000)
+    check_fields(lat, sim, tol=coherent_tol(3000))
+
+
+def test_noslip_channel_with_moving_reference():
+    """No-slip walls with a nonzero stored reference velocity (u_in): the
+    bounce-back swap must carry the reference-equilibrium difference."""
+    nx, ny = 40, 24
+    rng = np.random.default_rng(3)
+    ux = 0.03 + 0.002 * rng.standard_normal((ny, nx))
+    uy = 0.002 * rng.standard_normal((ny, nx))
+    rho = 1 + 0.001 * rng.standard_normal((ny, nx))
+    lat = B.Lattice(nx, ny, 0.7, u_in=0.03, bc_x=B.BTDF_BCX_PERIODIC, bc_y=B.BTDF_BCY_NOSLIP)
+    sim = O.Sim(nx, ny, 0.7, 0.03, 0, 2, 0.0, 0.0, 3, 1)
+    lat.init_fields(rho, ux, uy)
+    sim.init_fields(rho, ux, uy)
+    lat.step(300)
+    sim.step(300)
+    check_fields(lat, sim, tol=coherent_tol(300))
+
+
+def test_ragged_lattice_wrapping_body_and_g():
+    """nx not a multiple of the vector width, a body whose support wraps the
+    periodic x edge, free-slip walls and a uniform body force together."""
+    case = W.Case("ragged", 131, 37, 0.7, 0.0, 3, W.BCX_PERIODIC, W.BCY_FREESLIP,
+                  gx=2e-6, gy=0.0, seed=4, D=8.0, noise=1e-3)
+    case.u_in = 0.03
+    case.bodies = [W.circle_markers(1.2, 18.3, 8.0, 25), W.circle_markers(70.0, 15.1, 6.0, 19)]
+    lat, sim = run_both(case, 400)
+    check_fields(lat, sim)
+    for b in (0, 1):
+        check_forces(lat, sim, case, body=b)
+
+
+def test_many_bodies_channel():
+    case = W.Case("four", 200, 100, 0.6, W.U_IN, 3, W.BCX_INOUT, W.BCY_FREESLIP, seed=6, D=10.0)
+    for (x, y) in ((50, 30), (52, 70), (110, 50), (160, 25)):
+        case.bodies.append(W.circle_markers(x + 0.37, y + 0.21, 10.0, 31))
+    lat, sim = run_both(case, 500)
+    check_fields(lat, sim)
+    for b in range(4):
+        check_forces(lat, sim, case, body=b)
+
+
+@pytest.mark.parametrize("nf", [2, 4])
+def test_multi_direct_forcing(nf):
+    case = W.small_cylinder(delta=3, seed=7)
+    case.nf = nf
+    case.drs = 1.0
+    lat, sim = run_both(case, 300)
+    check_fields(lat, sim)
+    check_forces(lat, sim, case)
+
+
+def test_no_markers_and_tiny_lattice():
+    for (nx, ny) in ((4, 4), (5, 7), (33, 9)):
+        rng = np.random.default_rng(nx)
+        rho = 1 + 0.01 * rng.standard_normal((ny, nx))
+        ux = 0.02 * rng.standard_normal((ny, nx))
+        uy = 0.02 * rng.standard_normal((ny, nx))
+        for bcy in (0, 1, 2):
+            lat = B.Lattice(nx, ny, 0.8, bc_y=bcy)
+            sim = O.Sim(nx, ny, 0.8, 0.0, 0, bcy, 0.0, 0.0, 3, 1)
+            lat.init_fields(rho, ux, uy)
+            sim.init_fields(rho, ux, uy)
+            lat.step(50)
+            sim.step(50)
+            check_fields(lat, sim, tol=coherent_tol(50))
+            p = lat.field(B.FIELD_POPS)
+            P = sim.pops()
+            assert np.abs(p - P.transpose(2, 0, 1)).max() < 1e-6
+
+
+def test_zero_steps_and_populations_after_init():
+    case = W.small_cylinder(delta=3)
+    lat = B.Lattice.from_case(case)
+    sim = O.Sim.from_case(case)
+    lat.step(0)
+    p = lat.field(B.FIELD_POPS)
+    assert np.abs(p - sim.pops().transpose(2, 0, 1)).max() < 1e-7
+
+
+def test_checkpoint_roundtrip_is_exact():
+    case = W.small_cylinder(delta=3, seed=9)
+    a = B.Lattice.from_case(case)
+    a.step(37)
+    blob = a.save_state()
+    a.step(50)
+    ua = a.field(B.FIELD_UX)
+    b = B.Lattice.from_case(case)
+    b.load_state(blob)
+    assert b.steps == 37
+    b.step(50)
+    assert np.array_equal(ua, b.field(B.FIELD_UX))
+    # forces of steps before the checkpoint are not in b's history
+    with pytest.raises(B.BtdfError):
+        b.forces(0, 0, 10)
+    Fa = a.forces(0, 37, 50)
+    Fb = b.forces(0, 37, 50)
+    assert np.array_equal(Fa[0], Fb[0]) and np.array_equal(Fa[1], Fb[1])
+
+
+def test_graph_replay_matches_direct_launches():
+    case = W.small_cylinder(delta=4, seed=10)
+    a = B.Lattice.from_case(case)
+    b = B.Lattice.from_case(case)
+    a.step(200)                 # 1 local step, 3 graphs of 64, 7 direct
+    for _ in range(200):
+        b.step(1)               # direct launches only
+    assert np.array_equal(a.field(B.FIELD_UX), b.field(B.FIELD_UX))
+    assert np.array_equal(a.forces(0)[0], b.forces(0)[0])
+
+
+def test_history_ring_wraps():
+    case = W.small_cylinder(delta=3)
+    lat = B.Lattice.from_case(case, history_len=16)
+    sim = O.Sim.from_case(case)
+    lat.step(100)
+    sim.step(100)
+    gx, _ = lat.forces(0, 84, 16)
+    rx, _ = sim.history(0, 84, 16)
+    assert np.abs(gx - rx).max() <= 1e-4 * np.abs(rx).max()
+    with pytest.raises(B.BtdfError):
+        lat.forces(0, 83, 2)
+    with pytest.raises(B.BtdfError):
+        lat.forces(0, 99, 2)
+
+
+def test_moving_marker_velocity():
+    """Prescribed marker velocities (set through the C ABI) reach the force."""
+    case = W.small_cylinder(delta=3, seed=12)
+    lat = B.Lattice.from_case(case)
+    sim = O.Sim.from_case(case)
+    n = len(case.bodies[0].X)
+    ub = np.full(n, 0.01)
+    vb = np.linspace(-0.005, 0.005, n)
+    lat.set_marker_velocity(0, ub, vb)
+    sim.set_marker_velocity(0, ub, vb)
+    lat.step(200)
+    sim.step(200)
+    check_fields(lat, sim)
+    check_forces(lat, sim, case)
+
+
+def test_instability_is_reported():
+    n = 32
+    lat = B.Lattice(n, n, 0.5001)
+    rng = np.random.default_rng(0)
+    lat.init_fields(np.ones((n, n)), 0.4 * rng.standard_normal((n, n)),
+                    0.4 * rng.standard_normal((n, n)))
+    b = W.circle_markers(16, 16, 8, 25)
+    lat.add_markers(b.X, b.Y, b.ds)
+    lat.step(2000)
+    with pytest.raises(B.BtdfError) as ei:
+        lat.sync()
+    assert ei.value.status == B.BTDF_EUNSTABLE
+
+
+def test_device_pointer_readback():
+    case = W.small_cylinder(delta=3)
+    lat = B.Lattice.from_case(case)
+    lat.step(10)
+    t = torch.zeros((case.ny, case.nx), dtype=torch.float32, device="cuda")
+    lat.field_to_device(B.FIELD_UX, t.data_ptr())
+    assert np.array_equal(t.cpu().numpy(), lat.field(B.FIELD_UX))
