@@ -64,8 +64,10 @@ typedef enum {
     BTDF_DELTA4COS = 5
 } btdf_delta;
 
-/* Population storage.  All forms store deviations f - w_a from the lattice
- * weights; arithmetic is FP32 in every form. */
+/* Population storage.  All forms store deviations f_a - f_eq_a(1, (u_in, 0))
+ * from the equilibrium of the reference state (unit density, velocity
+ * (u_in, 0)), so rounding scales with the departure of the flow from that
+ * state; arithmetic is FP32 in every form. */
 typedef enum {
     BTDF_F32 = 0,
     BTDF_F16DEV = 1,
@@ -175,6 +177,20 @@ int btdf_load_state(btdf_ctx *ctx, const void *src, size_t len);
 int btdf_profile_enable(btdf_ctx *ctx, int32_t on);
 int btdf_profile_read(btdf_ctx *ctx, double *ms_ib, double *ms_lbm, int64_t *launches_ib,
                       int64_t *launches_lbm);
+
+/* Variant of the fused collide-stream kernel.  Results do not depend on it.
+ *   0 automatic (3 when tensor maps are available, else 1)
+ *   1 register-pipelined warps, 4 nodes per lane (16-byte FP32 vectors)
+ *   2 register-pipelined warps, 2 nodes per lane
+ *   3 TMA-tiled CTAs: 128 x 8 node tiles, 2 pipeline stages
+ *   4 TMA-tiled CTAs: 128 x 8 node tiles, 3 pipeline stages
+ *   5 TMA-tiled CTAs: 128 x 16 node tiles, 2 pipeline stages
+ *   6 register warps, 4 nodes per lane, next segment's loads issued early
+ *   7 register warps, 2 nodes per lane, next segment's loads issued early
+ * grid_blocks caps the persistent grid (0 = SM count x resident blocks per
+ * SM).  Synchronizes and drops cached CUDA graphs.
+ * Errors: EINVAL (unknown variant, TMA variant without tensor maps). */
+int btdf_tune(btdf_ctx *ctx, int32_t variant, int32_t grid_blocks);
 
 /* Bytes of device memory the context holds. */
 int btdf_device_bytes(const btdf_ctx *ctx, size_t *bytes);

@@ -30,7 +30,7 @@ EXPORTS = [
     "btdf_add_markers", "btdf_set_marker_velocity", "btdf_step", "btdf_sync",
     "btdf_read_forces", "btdf_read_markers", "btdf_read_field", "btdf_step_count",
     "btdf_state_size", "btdf_save_state", "btdf_load_state", "btdf_profile_enable",
-    "btdf_profile_read", "btdf_device_bytes", "btdf_last_error", "btdf_status_string",
+    "btdf_profile_read", "btdf_tune", "btdf_device_bytes", "btdf_last_error", "btdf_status_string",
     "btdf_version",
 ]
 
@@ -90,6 +90,7 @@ def lib() -> C.CDLL:
     L.btdf_profile_enable.argtypes = [ctxp, C.c_int32]
     L.btdf_profile_read.argtypes = [ctxp, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                     C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+    L.btdf_tune.argtypes = [ctxp, C.c_int32, C.c_int32]
     L.btdf_device_bytes.argtypes = [ctxp, C.POINTER(C.c_size_t)]
     L.btdf_last_error.argtypes = [ctxp]
     L.btdf_last_error.restype = C.c_char_p
@@ -252,6 +253,9 @@ class Lattice:
         self._check(lib().btdf_profile_read(self._ctx, C.byref(a), C.byref(b), C.byref(la),
                                             C.byref(lb)), "btdf_profile_read")
         return a.value, b.value, la.value, lb.value
+
+    def tune(self, nodes_per_lane=0, grid_blocks=0):
+        self._check(lib().btdf_tune(self._ctx, int(nodes_per_lane), int(grid_blocks)), "btdf_tune")
 
     def device_bytes(self) -> int:
         n = C.c_size_t()

@@ -7,6 +7,8 @@
 #include "btdf.h"
 #include "btdf_internal.cuh"
 
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -95,11 +97,17 @@ struct btdf_ctx {
     double* d_body_scale = nullptr;
     double2* d_hist = nullptr;
     unsigned long long* d_step = nullptr;
-    unsigned int* d_ticket = nullptr;
     int* d_status = nullptr;
     std::vector<MarkerAux> aux_host;
 
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    long long lbm_grid[2][2] = {{1, 1}, {1, 1}};   // persistent LBM grid [npl 4/2][local/pull]
+    long long pf_grid[2] = {1, 1};                 // software-pipelined kernel [npl 4/2]
+    long long tma_grid[kVarCount] = {};  // persistent grid of each TMA variant
+    int variant = kVarAuto;              // LBM kernel variant (btdf_tune)
+    int grid_override = 0;               // 0: SMs x resident blocks
+    bool tma_ok = false;                 // tensor maps encoded
+    CUtensorMap tmap[2][2];              // [buffer][box of 10 / 18 rows]
 
     bool prof = false;
     std::vector<cudaEvent_t> ev;         // 3 per profiled step
@@ -169,6 +177,8 @@ void free_markers(btdf_ctx* ctx) {
     dfree(ctx, ctx->d_hist);
 }
 
+bool is_tma(int v) { return v == kVarTma8x2 || v == kVarTma8x3 || v == kVarTma16x2; }
+
 LatticeParams lattice_params(const btdf_ctx* ctx) {
     LatticeParams p{};
     p.nx = ctx->cfg.nx;
@@ -183,6 +193,21 @@ LatticeParams lattice_params(const btdf_ctx* ctx) {
     p.u_in = (float)ctx->cfg.u_in;
     p.urx = (float)ctx->cfg.u_in;   // reference velocity of the stored deviations
     p.ury = 0.0f;
+    {
+        const double tau = ctx->cfg.tau, Ux = ctx->cfg.u_in, Uy = 0.0;
+        p.one_m_omega = (float)(1.0 - 1.0 / tau);
+        for (int a = 0; a < 9; a++) {
+            const double w = a == 0 ? 4.0 / 9.0 : (a < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+            const double eU = ex(a) * Ux + ey(a) * Uy;
+            p.eur[a] = (float)eU;
+            p.c1[a] = (float)(3.0 + 9.0 * eU);
+            p.kr[a] = (float)(1.0 + 3.0 * eU + 4.5 * eU * eU - 1.5 * (Ux * Ux + Uy * Uy));
+            p.wom[a] = (float)(w / tau);
+            p.wg[a] = (float)(w * (1.0 - 0.5 / tau));
+        }
+    }
+    p.nwork = (long long)ctx->cfg.ny * ctx->nseg;
+    for (int a = 0; a < 9; a++) p.poff[a] = (unsigned)(a * ctx->plane);
     p.gx = (float)ctx->cfg.gx;
     p.gy = (float)ctx->cfg.gy;
     p.seg_index = ctx->nmark > 0 ? ctx->d_seg_index : nullptr;
@@ -190,6 +215,12 @@ LatticeParams lattice_params(const btdf_ctx* ctx) {
     p.csr = ctx->d_csr;
     p.F = ctx->d_F[(ctx->cfg.nf - 1) % 2];
     p.step = ctx->d_step;
+    p.status = ctx->d_status;
+    p.nbody = ctx->nmark > 0 ? (int)ctx->bodies.size() : 0;
+    p.hist_len = ctx->cfg.history_len;
+    p.body_ptr = ctx->d_body_ptr;
+    p.body_scale = ctx->d_body_scale;
+    p.hist = ctx->d_hist;
     return p;
 }
 
@@ -217,7 +248,6 @@ int enqueue_step(btdf_ctx* ctx, cudaStream_t st, bool pull, int cur, bool prof) 
         for (int k = 1; k <= ctx->cfg.nf; k++) {
             IbParams q{};
             q.nmark = ctx->nmark;
-            q.nbody = (int)ctx->bodies.size();
             q.mk = ctx->d_mk;
             q.aux = ctx->d_aux;
             q.F_prev = k == 1 ? nullptr : ctx->d_F[(k - 2) % 2];
@@ -225,19 +255,33 @@ int enqueue_step(btdf_ctx* ctx, cudaStream_t st, bool pull, int cur, bool prof) 
             q.Us = ctx->d_Us;
             q.rhol = ctx->d_rhol;
             q.first_pass = k == 1;
-            q.last_pass = k == ctx->cfg.nf;
-            q.body_ptr = ctx->d_body_ptr;
-            q.body_scale = ctx->d_body_scale;
-            q.hist = ctx->d_hist;
-            q.hist_len = ctx->cfg.history_len;
-            q.step = ctx->d_step;
-            q.ticket = ctx->d_ticket;
             q.status = ctx->d_status;
             CK(launch_ib_force(ctx->cfg.storage, pull, ctx->width, ctx->g[cur], p, q, st));
         }
     }
     if (prof) CK(cudaEventRecord(e1, st));
-    CK(launch_collide_stream(ctx->cfg.storage, pull, ctx->g[cur], ctx->g[1 - cur], p, st));
+    // Without profiling events in between, the LBM kernel is a programmatic
+    // dependent of the IB kernel: its band nodes wait for the forces, the rest
+    // of the lattice overlaps the IB stage.
+    const bool pdl = ctx->nmark > 0 && !prof;
+    int v = ctx->variant == kVarAuto ? (ctx->tma_ok ? kVarTma8x2 : kVarReg4) : ctx->variant;
+    if (is_tma(v) && (!pull || !ctx->tma_ok)) v = kVarReg4;   // TMA kernel pulls only
+    if (is_tma(v)) {
+        const int grid = ctx->grid_override > 0 ? ctx->grid_override : (int)ctx->tma_grid[v];
+        CK(launch_collide_stream_tma(ctx->cfg.storage, v, &ctx->tmap[cur][v == kVarTma16x2 ? 1 : 0],
+                                     ctx->g[cur], ctx->g[1 - cur], p, grid, pdl, st));
+    } else if ((v == kVarReg4Pf || v == kVarReg2Pf) && pull) {
+        const int npl = v == kVarReg2Pf ? 2 : 4;
+        const int grid = ctx->grid_override > 0 ? ctx->grid_override : (int)ctx->pf_grid[npl == 2 ? 1 : 0];
+        CK(launch_collide_stream(ctx->cfg.storage, true, -npl, ctx->g[cur], ctx->g[1 - cur], p, grid,
+                                 pdl, st));
+    } else {
+        const int npl = (v == kVarReg2 || v == kVarReg2Pf) ? 2 : 4;
+        const int grid = ctx->grid_override > 0 ? ctx->grid_override
+                                                : (int)ctx->lbm_grid[npl == 2 ? 1 : 0][pull ? 1 : 0];
+        CK(launch_collide_stream(ctx->cfg.storage, pull, npl, ctx->g[cur], ctx->g[1 - cur], p, grid,
+                                 pdl, st));
+    }
     if (prof) CK(cudaEventRecord(e2, st));
     return BTDF_OK;
 }
@@ -262,6 +306,39 @@ int ensure_graph(btdf_ctx* ctx, int cur) {
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
     return BTDF_OK;
+}
+
+// 3-D tensor maps (x, y, population) of both population buffers for the
+// TMA-tiled LBM kernel.  Failure leaves the register-pipelined kernels in use.
+bool encode_tensor_maps(btdf_ctx* ctx) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || fn == nullptr) {
+        cudaGetLastError();
+        return false;
+    }
+    auto encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    const CUtensorMapDataType dt = ctx->cfg.storage == kStoreF32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : ctx->cfg.storage == kStoreF16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                                   : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const cuuint64_t dims[3] = {(cuuint64_t)ctx->nxp, (cuuint64_t)ctx->cfg.ny, 9};
+    const cuuint64_t strides[2] = {(cuuint64_t)ctx->nxp * ctx->elem,
+                                   (cuuint64_t)ctx->plane * ctx->elem};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const int rows[2] = {tma_box_rows(kVarTma8x2), tma_box_rows(kVarTma16x2)};
+    for (int b = 0; b < 2; b++)
+        for (int r = 0; r < 2; r++) {
+            const cuuint32_t box[3] = {(cuuint32_t)(kSeg + 2 * tma_halo(ctx->cfg.storage)),
+                                       (cuuint32_t)rows[r], 9};
+            if (encode(&ctx->tmap[b][r], dt, 3, ctx->g[b], dims, strides, box, estr,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+                CUDA_SUCCESS)
+                return false;
+        }
+    return true;
 }
 
 int read_status(btdf_ctx* ctx) {
@@ -451,7 +528,9 @@ int btdf_create(const btdf_config* cfg, void* stream, btdf_ctx** out) {
     if (!cfg || !out) return BTDF_EINVAL;
     *out = nullptr;
     const btdf_config& c = *cfg;
-    if (c.nx < 4 || c.ny < 4 || (long long)c.nx * c.ny > (1ll << 31)) return BTDF_EINVAL;
+    // element offsets inside the kernels are 32-bit: 9 planes of the padded lattice
+    if (c.nx < 4 || c.ny < 4) return BTDF_EINVAL;
+    if (9ll * (((long long)c.nx + 31) / 32 * 32) * c.ny >= (1ll << 32)) return BTDF_EINVAL;
     if (!(c.tau > 0.5) || !std::isfinite(c.tau)) return BTDF_EINVAL;
     if (support_width(c.delta) == 0) return BTDF_EINVAL;
     if (c.nf < 1 || c.nf > 64) return BTDF_EINVAL;
@@ -476,6 +555,20 @@ int btdf_create(const btdf_config* cfg, void* stream, btdf_ctx** out) {
     };
     cudaError_t e = cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) return bail(BTDF_ECUDA);
+    {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return bail(BTDF_ECUDA);
+        for (int v = 0; v < 2; v++)
+            for (int pull = 0; pull < 2; pull++)
+                ctx->lbm_grid[v][pull] =
+                    (long long)sms * collide_stream_blocks_per_sm(c.storage, pull != 0, v == 0 ? 4 : 2);
+        for (int v = 0; v < kVarCount; v++)
+            if (is_tma(v)) ctx->tma_grid[v] = (long long)sms * collide_stream_tma_blocks_per_sm(c.storage, v);
+        ctx->pf_grid[0] = (long long)sms * collide_stream_blocks_per_sm(c.storage, true, -4);
+        ctx->pf_grid[1] = (long long)sms * collide_stream_blocks_per_sm(c.storage, true, -2);
+    }
     const size_t bytes = (size_t)9 * ctx->plane * ctx->elem;
     for (int i = 0; i < 2; i++) {
         e = dalloc(ctx, &ctx->g[i], bytes);
@@ -483,12 +576,13 @@ int btdf_create(const btdf_config* cfg, void* stream, btdf_ctx** out) {
         if (e != cudaSuccess) return bail(BTDF_ECUDA);
         if (cudaMemsetAsync(ctx->g[i], 0, bytes, ctx->stream) != cudaSuccess) return bail(BTDF_ECUDA);
     }
+    ctx->tma_ok = encode_tensor_maps(ctx);
+    for (int v = 0; v < kVarCount; v++)
+        if (is_tma(v) && ctx->tma_grid[v] <= 0) ctx->tma_ok = false;
     if (dalloc(ctx, &ctx->d_step, sizeof(unsigned long long)) != cudaSuccess ||
-        dalloc(ctx, &ctx->d_ticket, sizeof(unsigned int)) != cudaSuccess ||
         dalloc(ctx, &ctx->d_status, sizeof(int)) != cudaSuccess)
         return bail(BTDF_ECUDA);
     if (cudaMemsetAsync(ctx->d_step, 0, sizeof(unsigned long long), ctx->stream) != cudaSuccess ||
-        cudaMemsetAsync(ctx->d_ticket, 0, sizeof(unsigned int), ctx->stream) != cudaSuccess ||
         cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream) != cudaSuccess ||
         cudaStreamSynchronize(ctx->stream) != cudaSuccess)
         return bail(BTDF_ECUDA);
@@ -504,7 +598,6 @@ int btdf_destroy(btdf_ctx* ctx) {
     dfree(ctx, ctx->g[0]);
     dfree(ctx, ctx->g[1]);
     dfree(ctx, ctx->d_step);
-    dfree(ctx, ctx->d_ticket);
     dfree(ctx, ctx->d_status);
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
     if (ctx->cap) cudaStreamDestroy(ctx->cap);
@@ -784,6 +877,19 @@ int btdf_profile_read(btdf_ctx* ctx, double* ms_ib, double* ms_lbm, int64_t* lau
     if (ms_lbm) *ms_lbm = b;
     if (launches_ib) *launches_ib = ctx->nmark > 0 ? nst * ctx->cfg.nf : 0;
     if (launches_lbm) *launches_lbm = nst;
+    return BTDF_OK;
+}
+
+int btdf_tune(btdf_ctx* ctx, int32_t variant, int32_t grid_blocks) {
+    if (!ctx) return BTDF_EINVAL;
+    if (variant < 0 || variant >= kVarCount) return fail(ctx, BTDF_EINVAL, "unknown kernel variant");
+    if (is_tma(variant) && !ctx->tma_ok)
+        return fail(ctx, BTDF_EINVAL, "TMA variants unavailable (tensor maps not encoded)");
+    if (grid_blocks < 0) return fail(ctx, BTDF_EINVAL, "grid_blocks < 0");
+    CK(cudaStreamSynchronize(ctx->stream));
+    drop_graphs(ctx);
+    ctx->variant = variant;
+    ctx->grid_override = grid_blocks;
     return BTDF_OK;
 }
 

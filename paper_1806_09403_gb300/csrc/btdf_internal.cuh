@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
@@ -69,45 +70,79 @@ struct CsrEntry {
 struct LatticeParams {
     int nx, ny, nxp, nseg;
     long long plane;           // elements per population plane (nxp * ny)
+    long long nwork;           // warp row segments of the LBM kernel
+    unsigned poff[9];          // a * plane: element offset of each population plane
     int bcx, bcy;
     float omega;               // 1 / tau
+    float one_m_omega;         // 1 - 1 / tau
     float guo;                 // 1 - 1 / (2 tau)
     float u_in;
     // Reference velocity U_r = (urx, ury): the buffers store
     // d_a = f_a - f_eq_a(1, U_r), so FP32 rounding scales with the departure
     // of the flow from the free stream rather than with the flow itself.
     float urx, ury;
+    // Per-population constants of the collision in that form:
+    //   c1 = 3 + 9 e.U_r,  k = 1 + P_a(U_r),  wom = w_a / tau,  wg = w_a (1 - 1/(2 tau)).
+    float eur[9], c1[9], kr[9], wom[9], wg[9];
     float gx, gy;              // uniform body force
     const int* seg_index;      // [ny * nseg] band segment id or -1 (null: no band)
     const int* seg_ptr;        // [nband * (kSeg + 1)] CSR row pointers per node
     const CsrEntry* csr;
     const float2* F;           // Lagrangian forces of the step (sum of passes)
     unsigned long long* step;  // device step counter, advanced by the LBM kernel
+    int* status;               // sticky device status bits
+    // Force on each body (Eq. 27), reduced in FP64 by block 0 of the LBM kernel.
+    int nbody;
+    int hist_len;
+    const int* body_ptr;       // [nbody + 1] marker ranges
+    const double* body_scale;  // ds * drs per body
+    double2* hist;             // [hist_len * nbody]
 };
 
 struct IbParams {
-    int nmark, nbody;
+    int nmark;
     const Marker* mk;
     const MarkerAux* aux;
     const float2* F_prev;      // forces accumulated by earlier passes (null on pass 1)
     float2* F_out;             // F_prev + this pass's increment
     float2* Us;                // D_I u* of pass 1 (diagnostic)
     float* rhol;               // D_I rho (diagnostic)
-    int first_pass, last_pass;
-    const int* body_ptr;       // [nbody + 1] marker ranges
-    const double* body_scale;  // ds * drs per body
-    double2* hist;             // [hist_len * nbody] force on each body per step
-    int hist_len;
-    const unsigned long long* step;
-    unsigned int* ticket;      // last-block-done counter, returned to 0 by that block
+    int first_pass;
     int* status;               // sticky device status bits
 };
 
 enum : int { kStatusUnstable = 1, kStatusTimeout = 2 };
 
 // Launchers implemented in btdf_kernels.cu.
-cudaError_t launch_collide_stream(int storage, bool pull, const void* gin, void* gout,
-                                  const LatticeParams& p, cudaStream_t st);
+// npl: nodes per lane (4 or 2; -4 / -2: software-pipelined kernel, pull
+// steps only); grid: upper bound on the blocks of the
+// persistent LBM kernel; pdl: launch as a programmatic dependent of the
+// preceding IB kernel (its non-band work overlaps the IB stage).
+cudaError_t launch_collide_stream(int storage, bool pull, int npl, const void* gin, void* gout,
+                                  const LatticeParams& p, int grid, bool pdl, cudaStream_t st);
+int collide_stream_blocks_per_sm(int storage, bool pull, int npl);
+
+// Kernel variants of the LBM step (btdf_tune): register-pipelined warps with
+// 4 or 2 nodes per lane, or TMA-tiled CTAs (tile rows x pipeline stages).
+enum : int {
+    kVarAuto = 0,
+    kVarReg4 = 1,
+    kVarReg2 = 2,
+    kVarTma8x2 = 3,
+    kVarTma8x3 = 4,
+    kVarTma16x2 = 5,
+    kVarReg4Pf = 6,
+    kVarReg2Pf = 7,
+    kVarCount = 8
+};
+// map: 3-D tensor map (x, y, population) of the input buffer with box
+// (128 + 2 * tma_halo(storage), tma_box_rows(variant), 9).
+cudaError_t launch_collide_stream_tma(int storage, int variant, const CUtensorMap* map, const void* gin,
+                                      void* gout, const LatticeParams& p, int grid, bool pdl,
+                                      cudaStream_t st);
+int collide_stream_tma_blocks_per_sm(int storage, int variant);
+int tma_box_rows(int variant);
+int tma_halo(int storage);
 cudaError_t launch_ib_force(int storage, bool pull, int width, const void* g,
                             const LatticeParams& p, const IbParams& q, cudaStream_t st);
 cudaError_t launch_init_equilibrium(int storage, void* g, const LatticeParams& p,

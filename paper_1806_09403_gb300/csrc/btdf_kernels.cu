@@ -22,6 +22,10 @@
 //                  (Eq. 7), BGK collision (Eq. 5), vector stores.
 #include "btdf_internal.cuh"
 
+#include <cuda.h>
+
+#include <algorithm>
+
 namespace btdf {
 namespace {
 
@@ -31,52 +35,92 @@ constexpr unsigned kFull = 0xffffffffu;
 
 template <typename T> struct Io;
 
+// FP32 storage: N = 4 -> one 16-byte vector, N = 2 -> one 8-byte vector.
 template <> struct Io<float> {
-    static __device__ __forceinline__ float4 ld4(const float* p) {
-        return __ldg(reinterpret_cast<const float4*>(p));
+    template <int N>
+    static __device__ __forceinline__ void ldv(const float* p, float (&o)[N]) {
+        if constexpr (N == 4) {
+            const float4 v = *reinterpret_cast<const float4*>(p);
+            o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+        } else {
+            const float2 v = *reinterpret_cast<const float2*>(p);
+            o[0] = v.x; o[1] = v.y;
+        }
+    }
+    template <int N>
+    static __device__ __forceinline__ void stv(float* p, const float (&o)[N]) {
+        if constexpr (N == 4) *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+        else *reinterpret_cast<float2*>(p) = make_float2(o[0], o[1]);
     }
     static __device__ __forceinline__ float ld1(const float* p) { return __ldg(p); }
-    static __device__ __forceinline__ void st4(float* p, float4 v) {
-        *reinterpret_cast<float4*>(p) = v;
-    }
-    static __device__ __forceinline__ float cvt(float v) { return v; }
+    static __device__ __forceinline__ float ld1s(const float* p) { return *p; }
 };
 
-template <> struct Io<__half> {
-    static __device__ __forceinline__ float4 ld4(const __half* p) {
-        uint2 r = __ldg(reinterpret_cast<const uint2*>(p));
-        float2 a = __half22float2(*reinterpret_cast<__half2*>(&r.x));
-        float2 b = __half22float2(*reinterpret_cast<__half2*>(&r.y));
-        return make_float4(a.x, a.y, b.x, b.y);
-    }
-    static __device__ __forceinline__ float ld1(const __half* p) { return __half2float(__ldg(p)); }
-    static __device__ __forceinline__ void st4(__half* p, float4 v) {
-        __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);
-        uint2 r;
-        r.x = *reinterpret_cast<unsigned*>(&a);
-        r.y = *reinterpret_cast<unsigned*>(&b);
-        *reinterpret_cast<uint2*>(p) = r;
-    }
+// 16-bit storage (FP16 or BF16): pairs converted with the paired intrinsics.
+template <typename H, typename H2> struct Io16 {
+    static __device__ __forceinline__ float2 to2(unsigned u);
+    static __device__ __forceinline__ unsigned from2(float a, float b);
 };
+template <> __device__ __forceinline__ float2 Io16<__half, __half2>::to2(unsigned u) {
+    return __half22float2(*reinterpret_cast<const __half2*>(&u));
+}
+template <> __device__ __forceinline__ unsigned Io16<__half, __half2>::from2(float a, float b) {
+    const __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<const unsigned*>(&h);
+}
+template <> __device__ __forceinline__ float2 Io16<__nv_bfloat16, __nv_bfloat162>::to2(unsigned u) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u));
+}
+template <> __device__ __forceinline__ unsigned Io16<__nv_bfloat16, __nv_bfloat162>::from2(float a,
+                                                                                             float b) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const unsigned*>(&h);
+}
 
-template <> struct Io<__nv_bfloat16> {
-    static __device__ __forceinline__ float4 ld4(const __nv_bfloat16* p) {
-        uint2 r = __ldg(reinterpret_cast<const uint2*>(p));
-        float2 a = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&r.x));
-        float2 b = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&r.y));
-        return make_float4(a.x, a.y, b.x, b.y);
+template <typename H, typename H2> struct IoHalf {
+    using C = Io16<H, H2>;
+    template <int N>
+    static __device__ __forceinline__ void ldv(const H* p, float (&o)[N]) {
+        if constexpr (N == 4) {
+            const uint2 r = *reinterpret_cast<const uint2*>(p);
+            const float2 a = C::to2(r.x), b = C::to2(r.y);
+            o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+        } else {
+            const unsigned r = *reinterpret_cast<const unsigned*>(p);
+            const float2 a = C::to2(r);
+            o[0] = a.x; o[1] = a.y;
+        }
     }
-    static __device__ __forceinline__ float ld1(const __nv_bfloat16* p) {
-        return __bfloat162float(__ldg(p));
+    template <int N>
+    static __device__ __forceinline__ void stv(H* p, const float (&o)[N]) {
+        if constexpr (N == 4) {
+            uint2 r;
+            r.x = C::from2(o[0], o[1]);
+            r.y = C::from2(o[2], o[3]);
+            *reinterpret_cast<uint2*>(p) = r;
+        } else {
+            *reinterpret_cast<unsigned*>(p) = C::from2(o[0], o[1]);
+        }
     }
-    static __device__ __forceinline__ void st4(__nv_bfloat16* p, float4 v) {
-        __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
-        uint2 r;
-        r.x = *reinterpret_cast<unsigned*>(&a);
-        r.y = *reinterpret_cast<unsigned*>(&b);
-        *reinterpret_cast<uint2*>(p) = r;
-    }
+    static __device__ __forceinline__ float ld1(const H* p);
+    static __device__ __forceinline__ float ld1s(const H* p);
 };
+template <> __device__ __forceinline__ float IoHalf<__half, __half2>::ld1(const __half* p) {
+    return __half2float(__ldg(p));
+}
+template <> __device__ __forceinline__ float IoHalf<__nv_bfloat16, __nv_bfloat162>::ld1(
+    const __nv_bfloat16* p) {
+    return __bfloat162float(__ldg(p));
+}
+template <> __device__ __forceinline__ float IoHalf<__half, __half2>::ld1s(const __half* p) {
+    return __half2float(*p);
+}
+template <> __device__ __forceinline__ float IoHalf<__nv_bfloat16, __nv_bfloat162>::ld1s(
+    const __nv_bfloat16* p) {
+    return __bfloat162float(*p);
+}
+template <> struct Io<__half> : IoHalf<__half, __half2> {};
+template <> struct Io<__nv_bfloat16> : IoHalf<__nv_bfloat16, __nv_bfloat162> {};
 
 template <typename T>
 __device__ __forceinline__ void store_scalar(T* p, float v);
@@ -112,15 +156,18 @@ struct Moments {
     float drho, rho, inv, dux, duy;
 };
 
+// Every product that meets a sum is written as an explicit rounded operation
+// (__fmaf_rn, __fmul_rn), so the compiler cannot contract differently in
+// different kernels and all launch shapes give bitwise identical results.
 __device__ __forceinline__ Moments moments(const float d[9], float urx, float ury) {
     Moments m;
     m.drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
     m.rho = 1.0f + m.drho;
-    m.inv = 1.0f / m.rho;
+    m.inv = __fdividef(1.0f, m.rho);
     const float jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
     const float jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
-    m.dux = (jx - m.drho * urx) * m.inv;
-    m.duy = (jy - m.drho * ury) * m.inv;
+    m.dux = __fmul_rn(__fmaf_rn(-m.drho, urx, jx), m.inv);
+    m.duy = __fmul_rn(__fmaf_rn(-m.drho, ury, jy), m.inv);
     return m;
 }
 
@@ -204,65 +251,260 @@ __device__ __forceinline__ void read_node(const T* __restrict__ g, const Lattice
 
 // ---- the fused LBM kernel ----------------------------------------------------
 
-// One warp per 128-node row segment, 4 consecutive nodes per lane.  All nine
-// vector loads (and the one scalar per shifted plane that lane 0 / lane 31
-// needs from the neighbouring segment) are issued before any is used; the
-// values that cross lanes come by shuffle.  Row-end nodes are recomputed by
-// pull_node, which carries every boundary rule.
-template <typename T, bool kPull>
-__global__ void __launch_bounds__(kThreads)
-collide_stream_kernel(const T* __restrict__ gin, T* __restrict__ gout, LatticeParams p) {
-    const int lane = threadIdx.x & 31;
-    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (blockIdx.x == 0 && threadIdx.x == 0 && p.step != nullptr) *p.step += 1ull;
-    const int y = (int)(wid / p.nseg);
-    if (y >= p.ny) return;                       // whole warps only
-    const int s = (int)(wid - (long long)y * p.nseg);
-    const int x0 = s * kSeg + kNodesPerLane * lane;
-    const bool live = x0 < p.nxp;
+// Force on every body (Eq. 27) from the Lagrangian forces of this step, in
+// FP64, and the step counter.  Run by block 0 of the LBM kernel, which waits
+// for the IB kernel first.
+__device__ void body_forces_and_step(const LatticeParams& p) {
+    __shared__ unsigned long long s_step;
+    if (p.nbody > 0) cudaGridDependencySynchronize();
+    if (threadIdx.x == 0) s_step = p.step != nullptr ? *p.step : 0ull;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const long long slot = (long long)(s_step % (unsigned long long)(p.hist_len > 0 ? p.hist_len : 1)) *
+                           p.nbody;
+    for (int b = warp; b < p.nbody; b += nwarps) {
+        double sx = 0.0, sy = 0.0;
+        for (int k = p.body_ptr[b] + lane; k < p.body_ptr[b + 1]; k += 32) {
+            const float2 F = p.F[k];
+            sx += (double)F.x;
+            sy += (double)F.y;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            sx += __shfl_xor_sync(kFull, sx, off);
+            sy += __shfl_xor_sync(kFull, sy, off);
+        }
+        if (lane == 0) {
+            const double sc = p.body_scale[b];
+            p.hist[slot + b] = make_double2(-sx * sc, -sy * sc);
+        }
+    }
+    if (threadIdx.x == 0 && p.step != nullptr) *p.step = s_step + 1ull;
+}
 
-    float4 v[9];
-    float edge[9], add[9];
+// Second half of one lattice segment, shared by the LBM kernels: the spread
+// force on this lane's nodes, the moments, the collision and the stores.
+// f holds the post-streaming deviations of nodes x0 .. x0+NPL-1 of row y;
+// xw is the first node of the warp's segment.
+// Band segment of row y that holds node xw (-1: none); loaded by the callers
+// before their population loads so that its latency overlaps them.
+__device__ __forceinline__ int band_segment(const LatticeParams& p, int y, int xw) {
+    return p.seg_index != nullptr ? __ldg(p.seg_index + y * p.nseg + xw / kSeg) : -1;
+}
+
+template <typename T, int NPL>
+__device__ __forceinline__ void collide_store(float (&f)[9][NPL], T* __restrict__ gout,
+                                              const LatticeParams& p, int y, int xw, int x0,
+                                              bool live, int seg) {
+    const unsigned rowoff = (unsigned)y * (unsigned)p.nxp + (unsigned)x0;
+    // Force density on this lane's nodes: node-centric spread (Eq. 15) of the
+    // Lagrangian forces over band segments (after the IB kernel has finished),
+    // plus the uniform body force.
+    float Fx[NPL], Fy[NPL];
+#pragma unroll
+    for (int i = 0; i < NPL; i++) {
+        Fx[i] = 0.0f;
+        Fy[i] = 0.0f;
+    }
+    bool forced = (p.gx != 0.f) || (p.gy != 0.f);
+    {
+        const int bs = xw / kSeg;
+        if (seg >= 0) {
+            forced = true;
+            cudaGridDependencySynchronize();
+            if (live) {
+                const int* ptr = p.seg_ptr + (long long)seg * (kSeg + 1) + (x0 - bs * kSeg);
+#pragma unroll
+                for (int i = 0; i < NPL; i++) {
+                    const int b = __ldg(ptr + i), e = __ldg(ptr + i + 1);
+                    float sx = 0.f, sy = 0.f;
+                    for (int k = b; k < e; k++) {
+                        const CsrEntry c = p.csr[k];
+                        const float2 F = p.F[c.marker];
+                        sx = __fmaf_rn(c.w, F.x, sx);
+                        sy = __fmaf_rn(c.w, F.y, sy);
+                    }
+                    Fx[i] = sx;
+                    Fy[i] = sy;
+                }
+            }
+        }
+    }
+
+    // Moments (Eqs. 9-10) and the velocity correction u = u* + f / (2 rho)
+    // (Eq. 11), as deviations from the reference state.
+    float drho[NPL], rho[NPL], du[NPL], dv[NPL], pd0[NPL], uF[NPL];
+#pragma unroll
+    for (int i = 0; i < NPL; i++) {
+        float d[9];
+#pragma unroll
+        for (int a = 0; a < 9; a++) d[a] = f[a][i];
+        const Moments m = moments(d, p.urx, p.ury);
+        float a0 = m.dux, b0 = m.duy;
+        uF[i] = 0.0f;
+        if (forced) {
+            Fx[i] += p.gx;
+            Fy[i] += p.gy;
+            a0 = __fmaf_rn(__fmul_rn(0.5f, Fx[i]), m.inv, a0);
+            b0 = __fmaf_rn(__fmul_rn(0.5f, Fy[i]), m.inv, b0);
+            uF[i] = __fmaf_rn(p.urx + a0, Fx[i], __fmul_rn(p.ury + b0, Fy[i]));
+        }
+        drho[i] = m.drho;
+        rho[i] = m.rho;
+        du[i] = a0;
+        dv[i] = b0;
+        float t = __fmaf_rn(a0, a0, __fmul_rn(b0, b0));
+        t = __fmaf_rn(2.0f * p.urx, a0, t);
+        t = __fmaf_rn(2.0f * p.ury, b0, t);
+        pd0[i] = __fmul_rn(1.5f, t);
+    }
+
+    // Collision (Eqs. 5-7), one population at a time, in the form
+    //   d_eq / w = drho (1 + P(U_r)) + rho (P(u) - P(U_r))
+    //   P(u) - P(U_r) = ed (3 + 9 e.U_r + 4.5 ed) - 1.5 (2 U_r.du + du^2),  ed = e.du
+    //   d' = (1 - 1/tau) d + (w / tau) d_eq / w
+    //        + (1 - 1/(2 tau)) w [e.F (3 + 9 e.u) - 3 u.F]
+    T* const out = gout + rowoff;
+    const bool store = live && x0 < p.nx;
+    if (!forced) {
+#pragma unroll
+        for (int a = 0; a < 9; a++) {
+            float o[NPL];
+#pragma unroll
+            for (int i = 0; i < NPL; i++) {
+                const float ed = ex(a) * du[i] + ey(a) * dv[i];
+                const float pdiff = __fmaf_rn(ed, __fmaf_rn(4.5f, ed, p.c1[a]), -pd0[i]);
+                const float deqw = __fmaf_rn(rho[i], pdiff, __fmul_rn(p.kr[a], drho[i]));
+                o[i] = __fmaf_rn(p.wom[a], deqw, __fmul_rn(p.one_m_omega, f[a][i]));
+            }
+            if (store) Io<T>::template stv<NPL>(out + p.poff[a], o);
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < 9; a++) {
+            float o[NPL];
+#pragma unroll
+            for (int i = 0; i < NPL; i++) {
+                const float ed = ex(a) * du[i] + ey(a) * dv[i];
+                const float pdiff = __fmaf_rn(ed, __fmaf_rn(4.5f, ed, p.c1[a]), -pd0[i]);
+                const float deqw = __fmaf_rn(rho[i], pdiff, __fmul_rn(p.kr[a], drho[i]));
+                float r = __fmaf_rn(p.wom[a], deqw, __fmul_rn(p.one_m_omega, f[a][i]));
+                const float eF = ex(a) * Fx[i] + ey(a) * Fy[i];
+                const float eu = p.eur[a] + ed;
+                const float g = __fmaf_rn(eF, __fmaf_rn(9.0f, eu, 3.0f), __fmul_rn(-3.0f, uF[i]));
+                o[i] = __fmaf_rn(p.wg[a], g, r);
+            }
+            if (store) Io<T>::template stv<NPL>(out + p.poff[a], o);
+        }
+    }
+}
+
+// One row segment of 32 * NPL nodes: NPL consecutive nodes per lane.  All
+// nine vector loads (and the one scalar per shifted plane that lane 0 /
+// lane 31 needs from the neighbouring segment) are issued before any is used;
+// the values that cross lanes come by shuffle.  Row-end nodes are recomputed
+// by pull_node, which carries every boundary rule.  Offsets are 32-bit
+// element offsets (the lattice holds fewer than 2^32 / 9 nodes).
+template <typename T, bool kPull, int NPL>
+__device__ __forceinline__ void lbm_segment(const T* __restrict__ gin, T* __restrict__ gout,
+                                            const LatticeParams& p, int y, int xw, int lane) {
+    const int x0 = xw + NPL * lane;
+    const bool live = x0 < p.nxp;
+    const bool lane0 = lane == 0, lane31 = lane == 31;
+    const unsigned nxp = (unsigned)p.nxp;
+    const int seg = band_segment(p, y, xw);
+
+    float f[9][NPL];
+    if (!kPull || (y > 0 && y < p.ny - 1)) {
+        // Interior row: every source row is y - e_y and every shift -e_x is
+        // known at compile time.  Lanes past the padded row end load a valid
+        // vector and never store.
+        const int x0c = live ? x0 : p.nxp - NPL;
+        const unsigned rowc = (unsigned)y * nxp + (unsigned)x0c;
+#pragma unroll
+        for (int a = 0; a < 9; a++) {
+            const int dx = kPull ? -ex(a) : 0, dy = kPull ? -ey(a) : 0;
+            const unsigned off = p.poff[a] + rowc + (unsigned)(dy * (int)nxp);
+            Io<T>::template ldv<NPL>(gin + off, f[a]);
+            float edge = 0.0f;
+            if (dx < 0 && lane0 && x0 > 0) edge = Io<T>::ld1(gin + (off - 1));
+            if (dx > 0 && lane31 && x0 + NPL < p.nxp) edge = Io<T>::ld1(gin + (off + NPL));
+            if (dx < 0) {
+                float prev = __shfl_up_sync(kFull, f[a][NPL - 1], 1);
+                if (lane0) prev = edge;
+#pragma unroll
+                for (int i = NPL - 1; i > 0; i--) f[a][i] = f[a][i - 1];
+                f[a][0] = prev;
+            } else if (dx > 0) {
+                float next = __shfl_down_sync(kFull, f[a][0], 1);
+                if (lane31) next = edge;
+#pragma unroll
+                for (int i = 0; i < NPL - 1; i++) f[a][i] = f[a][i + 1];
+                f[a][NPL - 1] = next;
+            }
+        }
+    } else {
+    const unsigned rowoff = (unsigned)y * nxp + (unsigned)x0;
+    float edge[9];
     int shift[9];
 #pragma unroll
     for (int a = 0; a < 9; a++) {
-        const T* row;
+        unsigned off;
         int dx = 0;
-        add[a] = 0.0f;
         if (kPull) {
-            int pa, sy;
-            y_source(a, y, p, pa, sy, dx, add[a]);
-            row = gin + pa * p.plane + (long long)sy * p.nxp;
+            int pa = a, sy = y - ey(a);
+            dx = -ex(a);
+            if (sy < 0 || sy >= p.ny) {
+                float unused;
+                y_source(a, y, p, pa, sy, dx, unused);
+            }
+            off = p.poff[pa] + (unsigned)sy * nxp + (unsigned)x0;
         } else {
-            row = gin + a * p.plane + (long long)y * p.nxp;
+            off = p.poff[a] + rowoff;
         }
         shift[a] = dx;
-        v[a] = live ? Io<T>::ld4(row + x0) : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (live) {
+            Io<T>::template ldv<NPL>(gin + off, f[a]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < NPL; i++) f[a][i] = 0.0f;
+        }
         edge[a] = 0.0f;
-        if (dx < 0 && lane == 0 && live && x0 > 0) edge[a] = Io<T>::ld1(row + x0 - 1);
-        if (dx > 0 && lane == 31 && live && x0 + 4 < p.nxp) edge[a] = Io<T>::ld1(row + x0 + 4);
+        if (dx < 0 && lane0 && live && x0 > 0) edge[a] = Io<T>::ld1(gin + (off - 1));
+        if (dx > 0 && lane31 && live && x0 + NPL < p.nxp) edge[a] = Io<T>::ld1(gin + (off + NPL));
     }
-    float f[9][4];
 #pragma unroll
     for (int a = 0; a < 9; a++) {
-        float4 w = v[a];
         if (shift[a] < 0) {
-            float prev = __shfl_up_sync(kFull, w.w, 1);
-            if (lane == 0) prev = edge[a];
-            w = make_float4(prev, w.x, w.y, w.z);
-        } else if (shift[a] > 0) {
-            float next = __shfl_down_sync(kFull, w.x, 1);
-            if (lane == 31) next = edge[a];
-            w = make_float4(w.y, w.z, w.w, next);
-        }
-        f[a][0] = w.x + add[a];
-        f[a][1] = w.y + add[a];
-        f[a][2] = w.z + add[a];
-        f[a][3] = w.w + add[a];
-    }
-    if (kPull && live && (x0 == 0 || x0 + 3 >= p.nx - 1) && x0 < p.nx) {
+            float prev = __shfl_up_sync(kFull, f[a][NPL - 1], 1);
+            if (lane0) prev = edge[a];
 #pragma unroll
-        for (int i = 0; i < 4; i++) {
+            for (int i = NPL - 1; i > 0; i--) f[a][i] = f[a][i - 1];
+            f[a][0] = prev;
+        } else if (shift[a] > 0) {
+            float next = __shfl_down_sync(kFull, f[a][0], 1);
+            if (lane31) next = edge[a];
+#pragma unroll
+            for (int i = 0; i < NPL - 1; i++) f[a][i] = f[a][i + 1];
+            f[a][NPL - 1] = next;
+        }
+    }
+    }
+    if (kPull && p.bcy == kBcyNoslip && (y == 0 || y == p.ny - 1)) {
+        // bounce-back swapped these populations for their opposites
+#pragma unroll
+        for (int a = 0; a < 9; a++) {
+            const int sy = y - ey(a);
+            if (sy < 0 || sy >= p.ny) {
+                const float add = -6.0f * wt(a) * p.eur[a];
+#pragma unroll
+                for (int i = 0; i < NPL; i++) f[a][i] += add;
+            }
+        }
+    }
+    if (kPull && live && x0 < p.nx && (x0 == 0 || x0 + NPL - 1 >= p.nx - 1)) {
+#pragma unroll
+        for (int i = 0; i < NPL; i++) {
             const int x = x0 + i;
             if (x == 0 || x == p.nx - 1) {
                 float fe[9];
@@ -273,87 +515,359 @@ collide_stream_kernel(const T* __restrict__ gin, T* __restrict__ gout, LatticePa
         }
     }
 
-    // Force density on this lane's nodes: node-centric spread (Eq. 15) of the
-    // Lagrangian forces over band segments, plus the uniform body force.
-    float Fx[4], Fy[4];
-    bool forced = (p.gx != 0.f) || (p.gy != 0.f);
-#pragma unroll
-    for (int i = 0; i < 4; i++) {
-        Fx[i] = 0.0f;
-        Fy[i] = 0.0f;
+    collide_store<T, NPL>(f, gout, p, y, xw, x0, live, seg);
+}
+
+// Persistent grid: each warp walks the row segments with a grid stride,
+// stepping its (row, segment) pair without integer division.
+template <typename T, bool kPull, int NPL, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB)
+collide_stream_kernel(const T* __restrict__ gin, T* __restrict__ gout, LatticeParams p) {
+    if (blockIdx.x == 0) body_forces_and_step(p);
+    constexpr int SW = 32 * NPL;
+    const int lane = threadIdx.x & 31;
+    const int nsegw = (p.nxp + SW - 1) / SW;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int y = w0 / nsegw, s = w0 - y * nsegw;
+    const int dy = nw / nsegw, ds = nw - dy * nsegw;
+    while (y < p.ny) {
+        lbm_segment<T, kPull, NPL>(gin, gout, p, y, s * SW, lane);
+        s += ds;
+        y += dy;
+        if (s >= nsegw) {
+            s -= nsegw;
+            y += 1;
+        }
     }
-    if (p.seg_index != nullptr) {
-        const int seg = __ldg(p.seg_index + (long long)y * p.nseg + s);
-        if (seg >= 0) {
-            forced = true;
-            if (live) {
-                const int* ptr = p.seg_ptr + (long long)seg * (kSeg + 1) + kNodesPerLane * lane;
+}
+
+// ---- the software-pipelined LBM kernel ------------------------------------------
+
+// Raw loads of one interior row segment: the nine vectors and the one value
+// per shifted plane that lane 0 / lane 31 needs beyond the segment.
+template <int NPL>
+struct RawSeg {
+    float v[9][NPL];
+    float e[9];
+};
+
+template <typename T, int NPL>
+__device__ __forceinline__ void issue_interior(const T* __restrict__ gin, const LatticeParams& p, int y,
+                                               int xw, int lane, RawSeg<NPL>& r) {
+    const int x0 = xw + NPL * lane;
+    const int x0c = x0 < p.nxp ? x0 : p.nxp - NPL;
+    const unsigned nxp = (unsigned)p.nxp;
+    const unsigned rowc = (unsigned)y * nxp + (unsigned)x0c;
 #pragma unroll
-                for (int i = 0; i < 4; i++) {
-                    const int b = __ldg(ptr + i), e = __ldg(ptr + i + 1);
-                    for (int k = b; k < e; k++) {
-                        const CsrEntry c = p.csr[k];
-                        const float2 F = p.F[c.marker];
-                        Fx[i] += c.w * F.x;
-                        Fy[i] += c.w * F.y;
+    for (int a = 0; a < 9; a++) {
+        const int dx = -ex(a), dy = -ey(a);
+        const unsigned off = p.poff[a] + rowc + (unsigned)(dy * (int)nxp);
+        Io<T>::template ldv<NPL>(gin + off, r.v[a]);
+        r.e[a] = 0.0f;
+        if (dx < 0 && lane == 0 && x0 > 0) r.e[a] = Io<T>::ld1(gin + (off - 1));
+        if (dx > 0 && lane == 31 && x0 + NPL < p.nxp) r.e[a] = Io<T>::ld1(gin + (off + NPL));
+    }
+}
+
+template <int NPL>
+__device__ __forceinline__ void shift_interior(RawSeg<NPL>& r, int lane, float (&f)[9][NPL]) {
+#pragma unroll
+    for (int a = 0; a < 9; a++) {
+        const int dx = -ex(a);
+#pragma unroll
+        for (int i = 0; i < NPL; i++) f[a][i] = r.v[a][i];
+        if (dx < 0) {
+            float prev = __shfl_up_sync(kFull, f[a][NPL - 1], 1);
+            if (lane == 0) prev = r.e[a];
+#pragma unroll
+            for (int i = NPL - 1; i > 0; i--) f[a][i] = f[a][i - 1];
+            f[a][0] = prev;
+        } else if (dx > 0) {
+            float next = __shfl_down_sync(kFull, f[a][0], 1);
+            if (lane == 31) next = r.e[a];
+#pragma unroll
+            for (int i = 0; i < NPL - 1; i++) f[a][i] = f[a][i + 1];
+            f[a][NPL - 1] = next;
+        }
+    }
+}
+
+// Same schedule as collide_stream_kernel, but each warp issues the loads of
+// its next interior segment before computing the current one, so memory
+// latency overlaps arithmetic.  Wall rows take the direct path.
+template <typename T, int NPL>
+__global__ void __launch_bounds__(kThreads, 2)
+collide_stream_pf_kernel(const T* __restrict__ gin, T* __restrict__ gout, LatticeParams p) {
+    if (blockIdx.x == 0) body_forces_and_step(p);
+    constexpr int SW = 32 * NPL;
+    const int lane = threadIdx.x & 31;
+    const int nsegw = (p.nxp + SW - 1) / SW;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int y = w0 / nsegw, s = w0 - y * nsegw;
+    const int dy = nw / nsegw, ds = nw - dy * nsegw;
+    RawSeg<NPL> cur;
+    bool interior = y > 0 && y < p.ny - 1;
+    if (y < p.ny && interior) issue_interior<T, NPL>(gin, p, y, s * SW, lane, cur);
+    while (y < p.ny) {
+        int yn = y + dy, sn = s + ds;
+        if (sn >= nsegw) {
+            sn -= nsegw;
+            yn += 1;
+        }
+        const bool n_interior = yn > 0 && yn < p.ny - 1;
+        RawSeg<NPL> nxt;
+        if (yn < p.ny && n_interior) issue_interior<T, NPL>(gin, p, yn, sn * SW, lane, nxt);
+        const int xw = s * SW;
+        if (interior) {
+            const int x0 = xw + NPL * lane;
+            const bool live = x0 < p.nxp;
+            const int seg = band_segment(p, y, xw);
+            float f[9][NPL];
+            shift_interior<NPL>(cur, lane, f);
+            if (live && x0 < p.nx && (x0 == 0 || x0 + NPL - 1 >= p.nx - 1)) {
+#pragma unroll
+                for (int i = 0; i < NPL; i++) {
+                    const int x = x0 + i;
+                    if (x == 0 || x == p.nx - 1) {
+                        float fe[9];
+                        pull_node<T>(gin, p, x, y, fe);
+#pragma unroll
+                        for (int a = 0; a < 9; a++) f[a][i] = fe[a];
                     }
                 }
             }
+            collide_store<T, NPL>(f, gout, p, y, xw, x0, live, seg);
+        } else {
+            lbm_segment<T, true, NPL>(gin, gout, p, y, xw, lane);
         }
+        cur = nxt;
+        y = yn;
+        s = sn;
+        interior = n_interior;
     }
+}
 
-    // Moments and velocity correction u = u* + f / (2 rho) (Eq. 11).
-    float drho[4], rho[4], dux[4], duy[4], ux[4], uy[4], usq[4], pd0[4];
-#pragma unroll
-    for (int i = 0; i < 4; i++) {
-        float d[9];
-#pragma unroll
-        for (int a = 0; a < 9; a++) d[a] = f[a][i];
-        const Moments m = moments(d, p.urx, p.ury);
-        Fx[i] += p.gx;
-        Fy[i] += p.gy;
-        float du = m.dux, dv = m.duy;
-        if (forced) {
-            du += 0.5f * Fx[i] * m.inv;
-            dv += 0.5f * Fy[i] * m.inv;
+// ---- the TMA-tiled LBM kernel ---------------------------------------------------
+
+// Tiles of 128 nodes x TH rows.  One elected thread streams each tile's nine
+// population planes, with a one-row and a 16-byte-column halo, from global
+// into shared memory with a single 3-D cp.async.bulk.tensor load per tile;
+// S tiles are in flight per CTA, tracked by one mbarrier per stage.  Warp w
+// of the CTA then computes row y0 + w of the tile from shared memory (x and
+// y neighbours included) and stores its post-collision populations straight
+// to global memory with vector stores.  Nodes the tile cannot serve (periodic
+// wrap rows, the two row ends) fall back to global loads.
+template <typename T, int TH, int S>
+struct TmaCfg {
+    static constexpr int TW = kSeg;                  // 32 lanes x 4 nodes
+    static constexpr int H = 16 / (int)sizeof(T);    // halo columns: 16 bytes
+    static constexpr int BX = TW + 2 * H;
+    static constexpr int BY = TH + 2;
+    static constexpr int STAGE_BYTES = 9 * BY * BX * (int)sizeof(T);
+    static constexpr int STAGE_STRIDE = (STAGE_BYTES + 1023) / 1024 * 1024;
+    static constexpr int SMEM = S * STAGE_STRIDE + 1024 + 64;
+};
+
+// Wait bound for one stage (about a second of polling); past it the kernel
+// records a timeout and leaves instead of spinning on.
+constexpr unsigned kWaitLimit = 1u << 22;
+
+__device__ __forceinline__ unsigned smem_u32(const void* ptr) {
+    return (unsigned)__cvta_generic_to_shared(ptr);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n"
+        " .reg .pred p;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
+    for (unsigned i = 0; i < kWaitLimit; i++)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, unsigned long long* bar,
+                                            int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+template <typename T, int TH, int S>
+__device__ __forceinline__ void tma_issue(const CUtensorMap* map, unsigned char* stages,
+                                          unsigned long long* bars, int stage, int t, int ntx) {
+    using C = TmaCfg<T, TH, S>;
+    const int tx = t % ntx, ty = t / ntx;
+    mbar_expect_tx(&bars[stage], C::STAGE_BYTES);
+    // x starts 16 bytes left of the tile (aligned); rows start one above it.
+    // Coordinates off the lattice read as zero and are never used.
+    tma_load_3d(stages + stage * C::STAGE_STRIDE, map, &bars[stage], tx * C::TW - C::H, ty * TH - 1, 0);
+}
+
+template <typename T, int TH, int S>
+__global__ void __launch_bounds__(32 * TH, TH == 8 ? 2 : 1)
+collide_stream_tma_kernel(const __grid_constant__ CUtensorMap tmap, const T* __restrict__ gin,
+                          T* __restrict__ gout, LatticeParams p) {
+    using C = TmaCfg<T, TH, S>;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* stages =
+        (unsigned char*)(((unsigned long long)smem_raw + 1023ull) & ~1023ull);
+    unsigned long long* bars = (unsigned long long*)(stages + S * C::STAGE_STRIDE);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (blockIdx.x == 0) body_forces_and_step(p);
+
+    const int ntx = (p.nxp + C::TW - 1) / C::TW;
+    const int ntiles = ntx * ((p.ny + TH - 1) / TH);
+    if (tid == 0) {
+        for (int st = 0; st < S; st++) mbar_init(&bars[st], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int k = 0; k < S; k++) {
+            const int t = blockIdx.x + k * gridDim.x;
+            if (t < ntiles) tma_issue<T, TH, S>(&tmap, stages, bars, k, t, ntx);
         }
-        drho[i] = m.drho;
-        rho[i] = m.rho;
-        dux[i] = du;
-        duy[i] = dv;
-        ux[i] = p.urx + du;
-        uy[i] = p.ury + dv;
-        usq[i] = 1.5f * (ux[i] * ux[i] + uy[i] * uy[i]);
-        pd0[i] = 1.5f * (2.0f * (p.urx * du + p.ury * dv) + du * du + dv * dv);
-    }
 
-    // Collision (Eqs. 5-7) in deviation form, one population at a time:
-    //   d_eq = f_eq(rho, u) - f_eq(1, U_r) = w [drho (1 + P(u)) + P(u) - P(U_r)]
-    //   d'   = d - (d - d_eq) / tau + F_a
-    const long long base = (long long)y * p.nxp + x0;
-    const bool store = live && x0 < p.nx;
-#pragma unroll
-    for (int a = 0; a < 9; a++) {
-        const float eU = ex(a) * p.urx + ey(a) * p.ury;
-        float o[4];
-#pragma unroll
-        for (int i = 0; i < 4; i++) {
-            const float ed = ex(a) * dux[i] + ey(a) * duy[i];
-            const float eu = eU + ed;
-            const float pu = eu * (3.0f + 4.5f * eu) - usq[i];                 // P(u)
-            const float pdiff = ed * (3.0f + 4.5f * (2.0f * eU + ed)) - pd0[i];  // P(u) - P(U_r)
-            const float deq = wt(a) * (drho[i] * (1.0f + pu) + pdiff);            // Eq. 6
-            float r = f[a][i] - p.omega * (f[a][i] - deq);                        // Eq. 5
-            if (forced) {                                                         // Eq. 7
-                const float t = 3.0f * ((ex(a) - ux[i]) * Fx[i] + (ey(a) - uy[i]) * Fy[i]) +
-                                9.0f * eu * (ex(a) * Fx[i] + ey(a) * Fy[i]);
-                r += p.guo * wt(a) * t;
+    int issued = S;        // tiles whose loads were issued (bounded by ntiles below)
+    for (int k = 0;; k++) {
+        const int t = blockIdx.x + k * gridDim.x;
+        if (t >= ntiles) break;
+        const int st = k % S;
+        const bool ok = mbar_wait_bounded(&bars[st], (unsigned)((k / S) & 1));
+        if (!__syncthreads_and(ok)) {
+            // A copy did not land: record it and drain the others (bounded).
+            if (tid == 0) {
+                atomicOr(p.status, kStatusTimeout);
+                for (int j = k; j < issued; j++) {
+                    if (blockIdx.x + j * gridDim.x >= ntiles) break;
+                    mbar_wait_bounded(&bars[j % S], (unsigned)((j / S) & 1));
+                }
             }
-            o[i] = r;
+            return;
         }
-        if (store) Io<T>::st4(gout + a * p.plane + base, make_float4(o[0], o[1], o[2], o[3]));
+        const T* tile = (const T*)(stages + st * C::STAGE_STRIDE);
+        const int x0t = (t % ntx) * C::TW, y0 = (t / ntx) * TH;
+        const int y = y0 + warp;
+        if (y < p.ny) {
+            const int x0 = x0t + 4 * lane;
+            const bool live = x0 < p.nxp;
+            const int seg = band_segment(p, y, x0t);
+            float f[9][4];
+            if (y > 0 && y < p.ny - 1) {
+                // Interior row: all nine sources in the tile, shifts known at
+                // compile time.
+#pragma unroll
+                for (int a = 0; a < 9; a++) {
+                    const int dx = -ex(a);
+                    const T* srow = tile + (a * C::BY + warp + 1 - ey(a)) * C::BX + C::H;
+                    Io<T>::template ldv<4>(srow + 4 * lane, f[a]);
+                    if (dx < 0) {
+                        float prev = __shfl_up_sync(kFull, f[a][3], 1);
+                        if (lane == 0) prev = Io<T>::ld1s(srow - 1);
+                        f[a][3] = f[a][2]; f[a][2] = f[a][1]; f[a][1] = f[a][0]; f[a][0] = prev;
+                    } else if (dx > 0) {
+                        float next = __shfl_down_sync(kFull, f[a][0], 1);
+                        if (lane == 31) next = Io<T>::ld1s(srow + C::TW);
+                        f[a][0] = f[a][1]; f[a][1] = f[a][2]; f[a][2] = f[a][3]; f[a][3] = next;
+                    }
+                }
+            } else {
+#pragma unroll
+            for (int a = 0; a < 9; a++) {
+                int pa = a, sy = y - ey(a), dx = -ex(a);
+                if (sy < 0 || sy >= p.ny) {
+                    float unused;
+                    y_source(a, y, p, pa, sy, dx, unused);
+                }
+                const int r = sy - y0 + 1;                  // row inside the tile
+                float v[4];
+                if (r >= 0 && r < C::BY) {                  // from shared memory
+                    const T* srow = tile + (pa * C::BY + r) * C::BX + C::H;
+                    Io<T>::template ldv<4>(srow + 4 * lane, v);   // same bank group per lane
+                    if (dx < 0) {
+                        float prev = __shfl_up_sync(kFull, v[3], 1);
+                        if (lane == 0) prev = Io<T>::ld1s(srow - 1);
+                        v[3] = v[2]; v[2] = v[1]; v[1] = v[0]; v[0] = prev;
+                    } else if (dx > 0) {
+                        float next = __shfl_down_sync(kFull, v[0], 1);
+                        if (lane == 31) next = Io<T>::ld1s(srow + C::TW);
+                        v[0] = v[1]; v[1] = v[2]; v[2] = v[3]; v[3] = next;
+                    }
+                } else {                                    // periodic wrap row: global
+                    const T* grow = gin + p.poff[pa] + (unsigned)sy * (unsigned)p.nxp;
+                    if (live) Io<T>::template ldv<4>(grow + x0, v);
+                    else v[0] = v[1] = v[2] = v[3] = 0.0f;
+                    if (dx < 0) {
+                        float prev = __shfl_up_sync(kFull, v[3], 1);
+                        if (lane == 0) prev = (live && x0 > 0) ? Io<T>::ld1(grow + x0 - 1) : 0.0f;
+                        v[3] = v[2]; v[2] = v[1]; v[1] = v[0]; v[0] = prev;
+                    } else if (dx > 0) {
+                        float next = __shfl_down_sync(kFull, v[0], 1);
+                        if (lane == 31) next = (live && x0 + 4 < p.nxp) ? Io<T>::ld1(grow + x0 + 4) : 0.0f;
+                        v[0] = v[1]; v[1] = v[2]; v[2] = v[3]; v[3] = next;
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 4; i++) f[a][i] = v[i];
+            }
+            }
+            if (p.bcy == kBcyNoslip && (y == 0 || y == p.ny - 1)) {
+#pragma unroll
+                for (int a = 0; a < 9; a++) {
+                    const int sy = y - ey(a);
+                    if (sy < 0 || sy >= p.ny) {
+                        const float add = -6.0f * wt(a) * p.eur[a];
+#pragma unroll
+                        for (int i = 0; i < 4; i++) f[a][i] += add;
+                    }
+                }
+            }
+            if (live && x0 < p.nx && (x0 == 0 || x0 + 3 >= p.nx - 1)) {
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    const int x = x0 + i;
+                    if (x == 0 || x == p.nx - 1) {
+                        float fe[9];
+                        pull_node<T>(gin, p, x, y, fe);
+#pragma unroll
+                        for (int a = 0; a < 9; a++) f[a][i] = fe[a];
+                    }
+                }
+            }
+            collide_store<T, 4>(f, gout, p, y, x0t, x0, live, seg);
+        }
+        // Every thread is done with this stage: refill it with tile k + S.
+        __syncthreads();
+        if (tid == 0) {
+            const int t2 = blockIdx.x + (k + S) * gridDim.x;
+            if (t2 < ntiles) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                tma_issue<T, TH, S>(&tmap, stages, bars, st, t2, ntx);
+                issued = k + S + 1;
+            }
+        }
     }
-    (void)rho;
 }
 
 // ---- the IB stage -------------------------------------------------------------
@@ -361,16 +875,30 @@ collide_stream_kernel(const T* __restrict__ gin, T* __restrict__ gout, LatticePa
 // Lanes per marker: S*S support nodes rounded up to a power of two.
 template <int S> struct Group { static constexpr int G = (S * S <= 4) ? 4 : 16; };
 
+// Marker-parallel: one lane per support node, G lanes per marker.  Each lane
+// pulls the 9 populations of its node, forms rho and u* (Eqs. 9-10) and its
+// weighted share of the interpolation (Eq. 14); a segmented shuffle reduction
+// completes D_I rho and D_I u*, and the group's first lane writes
+// F_b = 2 rho_l (U_b - D_I u*) (Eq. 20).  The kernel lets the LBM kernel
+// launch at once: only band nodes there wait for these forces.
 template <typename T, int S>
 __global__ void __launch_bounds__(kThreads)
 ib_force_kernel(const T* __restrict__ g, LatticeParams p, IbParams q, int pull) {
+    cudaTriggerProgrammaticLaunchCompletion();
     constexpr int G = Group<S>::G;
     constexpr int MPW = 32 / G;
     const int lane = threadIdx.x & 31;
     const int li = lane % G;
     const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long m = wid * MPW + lane / G;
+    const bool head = li == 0 && m < q.nmark;
 
+    MarkerAux ax{};
+    float2 Fp = make_float2(0.f, 0.f);
+    if (head) {
+        ax = q.aux[m];
+        if (q.F_prev != nullptr) Fp = q.F_prev[m];
+    }
     // Weighted sums over the support (Eq. 14) of the density deviation and
     // of the velocity deviation u* - U_r.
     float wr = 0.f, wu = 0.f, wv = 0.f;
@@ -378,8 +906,8 @@ ib_force_kernel(const T* __restrict__ g, LatticeParams p, IbParams q, int pull) 
         const int xi = li % S, yi = li / S;
         const Marker* mk = q.mk + m;
         const float w = __ldg(&mk->w[li]);
+        const int x = __ldg(&mk->xs[xi]), y = __ldg(&mk->ys[yi]);
         if (w != 0.f) {
-            const int x = __ldg(&mk->xs[xi]), y = __ldg(&mk->ys[yi]);
             float d[9];
             read_node<T>(g, p, pull != 0, x, y, d);
             const Moments mo = moments(d, p.urx, p.ury);
@@ -395,8 +923,8 @@ ib_force_kernel(const T* __restrict__ g, LatticeParams p, IbParams q, int pull) 
                     for (int k = b; k < e; k++) {
                         const CsrEntry c = p.csr[k];
                         const float2 F = q.F_prev[c.marker];
-                        fx += c.w * F.x;
-                        fy += c.w * F.y;
+                        fx = __fmaf_rn(c.w, F.x, fx);
+                        fy = __fmaf_rn(c.w, F.y, fy);
                     }
                 }
                 du += 0.5f * fx * mo.inv;
@@ -413,58 +941,17 @@ ib_force_kernel(const T* __restrict__ g, LatticeParams p, IbParams q, int pull) 
         wu += __shfl_xor_sync(kFull, wu, off);
         wv += __shfl_xor_sync(kFull, wv, off);
     }
-    if (li == 0 && m < q.nmark) {
-        const MarkerAux ax = q.aux[m];
-        const float rl = ax.wsum + wr;                   // D_I rho
-        const float dFx = 2.0f * rl * (ax.ubx_rel - wu);   // Eq. 20 (dt = 1):
-        const float dFy = 2.0f * rl * (ax.uby_rel - wv);   // U_b - D_I u*, relative to U_r
-        float2 F = make_float2(dFx, dFy);
-        if (q.F_prev != nullptr) {
-            const float2 P = q.F_prev[m];
-            F.x += P.x;
-            F.y += P.y;
-        }
-        q.F_out[m] = F;
+    if (head) {
+        const float rl = ax.wsum + wr;                      // D_I rho
+        const float dFx = 2.0f * rl * (ax.ubx_rel - wu);    // Eq. 20 (dt = 1):
+        const float dFy = 2.0f * rl * (ax.uby_rel - wv);    // U_b - D_I u*, relative to U_r
+        q.F_out[m] = make_float2(Fp.x + dFx, Fp.y + dFy);
         if (q.first_pass) {
             q.Us[m] = make_float2(p.urx * ax.wsum + wu, p.ury * ax.wsum + wv);
             q.rhol[m] = rl;
         }
         if (!(rl > 0.f) || !isfinite(dFx) || !isfinite(dFy)) atomicOr(q.status, kStatusUnstable);
     }
-    if (!q.last_pass) return;
-
-    // Force on each body (Eq. 27), reduced in FP64 by the last block to finish.
-    __shared__ int s_last;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned t = atomicAdd(q.ticket, 1u);
-        s_last = (t == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    const unsigned long long step = *q.step;
-    const long long slot = (long long)(step % (unsigned long long)q.hist_len) * q.nbody;
-    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (int b = warp; b < q.nbody; b += nwarps) {
-        double sx = 0.0, sy = 0.0;
-        for (int k = q.body_ptr[b] + lane; k < q.body_ptr[b + 1]; k += 32) {
-            const float2 F = __ldcg(q.F_out + k);
-            sx += (double)F.x;
-            sy += (double)F.y;
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            sx += __shfl_xor_sync(kFull, sx, off);
-            sy += __shfl_xor_sync(kFull, sy, off);
-        }
-        if (lane == 0) {
-            const double sc = q.body_scale[b];
-            q.hist[slot + b] = make_double2(-sx * sc, -sy * sc);
-        }
-    }
-    if (threadIdx.x == 0) *q.ticket = 0u;
 }
 
 // ---- initialisation and read-back ------------------------------------------------
@@ -514,16 +1001,140 @@ inline unsigned blocks_for(long long threads) {
     return (unsigned)((threads + kThreads - 1) / kThreads);
 }
 
+template <int NPL> struct Variant;
+template <> struct Variant<4> { static constexpr int MINB = 3; };   // <= 80 registers
+template <> struct Variant<2> { static constexpr int MINB = 4; };   // <= 64 registers
+
+template <typename T, int NPL>
+cudaError_t collide_stream_tn(bool pull, const void* gin, void* gout, LatticeParams p, int grid,
+                              bool pdl, cudaStream_t st) {
+    constexpr int SW = 32 * NPL;
+    p.nwork = (long long)p.ny * ((p.nxp + SW - 1) / SW);
+    const long long need = (p.nwork * 32 + kThreads - 1) / kThreads;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)std::min<long long>(need, (long long)grid));
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    const T* a = (const T*)gin;
+    T* b = (T*)gout;
+    constexpr int MB = Variant<NPL>::MINB;
+    if (pull) return cudaLaunchKernelEx(&cfg, collide_stream_kernel<T, true, NPL, MB>, a, b, p);
+    return cudaLaunchKernelEx(&cfg, collide_stream_kernel<T, false, NPL, MB>, a, b, p);
+}
+
+template <typename T, int NPL>
+cudaError_t collide_stream_pf_tn(const void* gin, void* gout, LatticeParams p, int grid, bool pdl,
+                                 cudaStream_t st) {
+    constexpr int SW = 32 * NPL;
+    p.nwork = (long long)p.ny * ((p.nxp + SW - 1) / SW);
+    const long long need = (p.nwork * 32 + kThreads - 1) / kThreads;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)std::min<long long>(need, (long long)grid));
+    cfg.blockDim = dim3(kThreads);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, collide_stream_pf_kernel<T, NPL>, (const T*)gin, (T*)gout, p);
+}
+
+template <typename T, int NPL>
+int pf_blocks_tn() {
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, collide_stream_pf_kernel<T, NPL>, kThreads, 0);
+    return n;
+}
+
 template <typename T>
-cudaError_t collide_stream_t(bool pull, const void* gin, void* gout, const LatticeParams& p,
-                             cudaStream_t st) {
-    const long long threads = (long long)p.ny * p.nseg * 32;
-    const unsigned nb = blocks_for(threads);
+cudaError_t collide_stream_t(bool pull, int npl, const void* gin, void* gout, const LatticeParams& p,
+                             int grid, bool pdl, cudaStream_t st) {
+    if (pull && npl == -2) return collide_stream_pf_tn<T, 2>(gin, gout, p, grid, pdl, st);
+    if (pull && npl == -4) return collide_stream_pf_tn<T, 4>(gin, gout, p, grid, pdl, st);
+    if (npl < 0) npl = -npl;
+    if (npl == 2) return collide_stream_tn<T, 2>(pull, gin, gout, p, grid, pdl, st);
+    return collide_stream_tn<T, 4>(pull, gin, gout, p, grid, pdl, st);
+}
+
+template <typename T, int NPL>
+int blocks_per_sm_tn(bool pull) {
+    int n = 0;
+    constexpr int MB = Variant<NPL>::MINB;
     if (pull)
-        collide_stream_kernel<T, true><<<nb, kThreads, 0, st>>>((const T*)gin, (T*)gout, p);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, collide_stream_kernel<T, true, NPL, MB>,
+                                                      kThreads, 0);
     else
-        collide_stream_kernel<T, false><<<nb, kThreads, 0, st>>>((const T*)gin, (T*)gout, p);
-    return cudaGetLastError();
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, collide_stream_kernel<T, false, NPL, MB>,
+                                                      kThreads, 0);
+    return n > 0 ? n : 1;
+}
+
+template <typename T>
+int blocks_per_sm_t(bool pull, int npl) {
+    if (pull && npl == -2) return pf_blocks_tn<T, 2>();
+    if (pull && npl == -4) return pf_blocks_tn<T, 4>();
+    if (npl < 0) npl = -npl;
+    return npl == 2 ? blocks_per_sm_tn<T, 2>(pull) : blocks_per_sm_tn<T, 4>(pull);
+}
+
+template <typename T, int TH, int S>
+cudaError_t tma_tn(const CUtensorMap* map, const void* gin, void* gout, const LatticeParams& p,
+                   int grid, bool pdl, cudaStream_t st) {
+    using C = TmaCfg<T, TH, S>;
+    auto kern = collide_stream_tma_kernel<T, TH, S>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return e;
+    const long long ntiles = (long long)((p.nxp + C::TW - 1) / C::TW) * ((p.ny + TH - 1) / TH);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)std::min<long long>(ntiles, (long long)grid));
+    cfg.blockDim = dim3(32 * TH);
+    cfg.dynamicSmemBytes = C::SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, *map, (const T*)gin, (T*)gout, p);
+}
+
+template <typename T, int TH, int S>
+int tma_blocks_tn() {
+    using C = TmaCfg<T, TH, S>;
+    auto kern = collide_stream_tma_kernel<T, TH, S>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) != cudaSuccess)
+        return 0;
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, 32 * TH, C::SMEM);
+    return n;
+}
+
+template <typename T>
+cudaError_t tma_t(int variant, const CUtensorMap* map, const void* gin, void* gout,
+                  const LatticeParams& p, int grid, bool pdl, cudaStream_t st) {
+    switch (variant) {
+    case kVarTma8x2: return tma_tn<T, 8, 2>(map, gin, gout, p, grid, pdl, st);
+    case kVarTma8x3: return tma_tn<T, 8, 3>(map, gin, gout, p, grid, pdl, st);
+    case kVarTma16x2: return tma_tn<T, 16, 2>(map, gin, gout, p, grid, pdl, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T>
+int tma_blocks_t(int variant) {
+    switch (variant) {
+    case kVarTma8x2: return tma_blocks_tn<T, 8, 2>();
+    case kVarTma8x3: return tma_blocks_tn<T, 8, 3>();
+    case kVarTma16x2: return tma_blocks_tn<T, 16, 2>();
+    default: return 0;
+    }
 }
 
 template <typename T, int S>
@@ -549,13 +1160,43 @@ cudaError_t ib_force_t(bool pull, int width, const void* g, const LatticeParams&
 
 }  // namespace
 
-cudaError_t launch_collide_stream(int storage, bool pull, const void* gin, void* gout,
-                                  const LatticeParams& p, cudaStream_t st) {
+cudaError_t launch_collide_stream(int storage, bool pull, int npl, const void* gin, void* gout,
+                                  const LatticeParams& p, int grid, bool pdl, cudaStream_t st) {
     switch (storage) {
-    case kStoreF32: return collide_stream_t<float>(pull, gin, gout, p, st);
-    case kStoreF16: return collide_stream_t<__half>(pull, gin, gout, p, st);
-    case kStoreBF16: return collide_stream_t<__nv_bfloat16>(pull, gin, gout, p, st);
+    case kStoreF32: return collide_stream_t<float>(pull, npl, gin, gout, p, grid, pdl, st);
+    case kStoreF16: return collide_stream_t<__half>(pull, npl, gin, gout, p, grid, pdl, st);
+    case kStoreBF16: return collide_stream_t<__nv_bfloat16>(pull, npl, gin, gout, p, grid, pdl, st);
     default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_collide_stream_tma(int storage, int variant, const CUtensorMap* map, const void* gin,
+                                      void* gout, const LatticeParams& p, int grid, bool pdl,
+                                      cudaStream_t st) {
+    switch (storage) {
+    case kStoreF32: return tma_t<float>(variant, map, gin, gout, p, grid, pdl, st);
+    case kStoreF16: return tma_t<__half>(variant, map, gin, gout, p, grid, pdl, st);
+    case kStoreBF16: return tma_t<__nv_bfloat16>(variant, map, gin, gout, p, grid, pdl, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+int collide_stream_tma_blocks_per_sm(int storage, int variant) {
+    switch (storage) {
+    case kStoreF16: return tma_blocks_t<__half>(variant);
+    case kStoreBF16: return tma_blocks_t<__nv_bfloat16>(variant);
+    default: return tma_blocks_t<float>(variant);
+    }
+}
+
+int tma_box_rows(int variant) { return variant == kVarTma16x2 ? 18 : 10; }
+int tma_halo(int storage) { return storage == kStoreF32 ? 4 : 8; }
+
+int collide_stream_blocks_per_sm(int storage, bool pull, int npl) {
+    switch (storage) {
+    case kStoreF16: return blocks_per_sm_t<__half>(pull, npl);
+    case kStoreBF16: return blocks_per_sm_t<__nv_bfloat16>(pull, npl);
+    default: return blocks_per_sm_t<float>(pull, npl);
     }
 }
 
