@@ -48,6 +48,9 @@ def workload_case(name):
     if name == "large":
         return W.many_cylinders(), \
             "8192x4096 lattice, 400 cylinders D=20 (63 markers each), Re=200, 3-point delta"
+    if name == "mid":
+        return W.many_cylinders(nx=4096, ny=2048, count=100), \
+            "4096x2048 lattice, 100 cylinders D=20 (63 markers each), Re=200, 3-point delta"
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -208,8 +211,9 @@ def kernel_mode(args):
     from paper_1806_09403_gb300 import btdf as B
     case, desc = workload_case(args.workload)
     storage = {"f32": 0, "f16": 1, "bf16": 2}[args.storage]
+    layout = {"rows": B.LAYOUT_ROWS, "planes": B.LAYOUT_PLANES}[args.layout]
     lat = B.Lattice.from_case(case, storage=storage,
-                              stream=torch.cuda.current_stream().cuda_stream)
+                              stream=torch.cuda.current_stream().cuda_stream, layout=layout)
     lat.tune(args.variant, 0)
     lat.profile(True)          # direct launches, one event pair per kernel
     lat.step(args.warmup + args.steps)
@@ -235,8 +239,9 @@ def our_arm(args):
     case, desc = workload_case(args.workload)
     storage = {"f32": 0, "f16": 1, "bf16": 2}[args.storage]
     stream = torch.cuda.current_stream()
+    layout = {"rows": B.LAYOUT_ROWS, "planes": B.LAYOUT_PLANES}[args.layout]
     lat = B.Lattice.from_case(case, storage=storage, stream=stream.cuda_stream,
-                              history_len=max(args.steps + args.warmup + 64, 4096))
+                              history_len=max(args.steps + args.warmup + 64, 4096), layout=layout)
     nodes = case.nx * case.ny
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
@@ -384,7 +389,8 @@ def our_arm(args):
         "dtype": {0: "f32", 1: "f32 (f16 storage)", 2: "f32 (bf16 storage)"}[storage],
         "data": "synthetic",
         "config": {"workload": desc, "nx": case.nx, "ny": case.ny,
-                   "storage": args.storage, "markers": sum(len(b.X) for b in case.bodies),
+                   "storage": args.storage, "layout": args.layout,
+                   "markers": sum(len(b.X) for b in case.bodies),
                    "l2": "flushed before every timed step (512 MB written, then read back so "
                          "the lines left in L2 are clean); flush outside the per-step CUDA events",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -413,13 +419,14 @@ def main():
     ap.add_argument("--steps", type=int, default=10000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="paper", choices=["paper", "small", "large"])
+    ap.add_argument("--workload", default="paper", choices=["paper", "small", "mid", "large"])
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-seconds", type=float, default=90.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="bench", choices=["bench", "kernel"])
     ap.add_argument("--variant", type=int, default=0, choices=list(range(8)))
+    ap.add_argument("--layout", default="rows", choices=["rows", "planes"])
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

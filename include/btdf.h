@@ -82,6 +82,11 @@ typedef enum { BTDF_BCX_PERIODIC = 0, BTDF_BCX_INOUT = 1 } btdf_bc_x;
  * 0 and ny-1. */
 typedef enum { BTDF_BCY_PERIODIC = 0, BTDF_BCY_FREESLIP = 1, BTDF_BCY_NOSLIP = 2 } btdf_bc_y;
 
+/* Device layout of the population buffers (elements of the storage type):
+ * planes: [9][ny][nxp]; rows: [ny][9][nxp] (the nine planes of one row are
+ * adjacent), with nxp = nx rounded up to a multiple of 32. */
+typedef enum { BTDF_LAYOUT_PLANES = 0, BTDF_LAYOUT_ROWS = 1 } btdf_layout;
+
 typedef enum {
     BTDF_FIELD_RHO = 0,   /* density, Eq. 9 (ny*nx floats) */
     BTDF_FIELD_UX = 1,    /* unforced velocity u*, Eq. 10 (ny*nx floats) */
@@ -99,10 +104,12 @@ typedef struct {
     int32_t bc_x, bc_y;    /* btdf_bc_x, btdf_bc_y */
     int32_t history_len;   /* steps of body-force history kept on the device (>= 1) */
     double gx, gy;         /* uniform body force added to the IB force everywhere */
+    int32_t layout;        /* btdf_layout */
+    int32_t reserved;      /* must be 0 */
 } btdf_config;
 
 /* Fills *cfg with a 64 x 64 periodic FP32 lattice, tau = 0.6, 3-point delta,
- * nf = 1, history_len = 4096. */
+ * nf = 1, history_len = 4096, row-interleaved layout. */
 int btdf_config_default(btdf_config *cfg);
 
 /* Validates *cfg, allocates the two population buffers and per-context

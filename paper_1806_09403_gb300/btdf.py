@@ -23,6 +23,7 @@ BTDF_F32, BTDF_F16DEV, BTDF_BF16DEV = 0, 1, 2
 BTDF_BCX_PERIODIC, BTDF_BCX_INOUT = 0, 1
 BTDF_BCY_PERIODIC, BTDF_BCY_FREESLIP, BTDF_BCY_NOSLIP = 0, 1, 2
 FIELD_RHO, FIELD_UX, FIELD_UY, FIELD_POPS = 0, 1, 2, 3
+LAYOUT_PLANES, LAYOUT_ROWS = 0, 1
 
 # Every symbol include/btdf.h declares.
 EXPORTS = [
@@ -42,6 +43,7 @@ class btdf_config(C.Structure):
         ("delta", C.c_int32), ("nf", C.c_int32), ("storage", C.c_int32),
         ("bc_x", C.c_int32), ("bc_y", C.c_int32), ("history_len", C.c_int32),
         ("gx", C.c_double), ("gy", C.c_double),
+        ("layout", C.c_int32), ("reserved", C.c_int32),
     ]
 
 
@@ -132,8 +134,10 @@ class Lattice:
 
     def __init__(self, nx, ny, tau, u_in=0.0, delta=3, nf=1, storage=BTDF_F32,
                  bc_x=BTDF_BCX_PERIODIC, bc_y=BTDF_BCY_PERIODIC, gx=0.0, gy=0.0,
-                 history_len=4096, stream: int = 0):
+                 history_len=4096, stream: int = 0, layout=None):
         cfg = btdf_config_default()
+        if layout is not None:
+            cfg.layout = int(layout)
         cfg.nx, cfg.ny, cfg.tau, cfg.u_in = int(nx), int(ny), float(tau), float(u_in)
         cfg.delta, cfg.nf, cfg.storage = int(delta), int(nf), int(storage)
         cfg.bc_x, cfg.bc_y, cfg.history_len = int(bc_x), int(bc_y), int(history_len)
@@ -147,9 +151,10 @@ class Lattice:
         self.body_markers = []
 
     @classmethod
-    def from_case(cls, case, storage=BTDF_F32, stream: int = 0, history_len=4096, drs=None):
+    def from_case(cls, case, storage=BTDF_F32, stream: int = 0, history_len=4096, drs=None,
+                  layout=None):
         lat = cls(case.nx, case.ny, case.tau, case.u_in, case.delta, case.nf, storage,
-                  case.bc_x, case.bc_y, case.gx, case.gy, history_len, stream)
+                  case.bc_x, case.bc_y, case.gx, case.gy, history_len, stream, layout)
         lat.init_fields(*case.initial_fields())
         for b in case.bodies:
             lat.add_markers(b.X, b.Y, b.ds, b.Ubx, b.Uby, drs=case.drs if drs is None else drs)

@@ -34,7 +34,7 @@ struct Body {
 struct StateHeader {
     uint64_t magic;
     int32_t nx, ny, nxp, storage;
-    int32_t poststream, reserved;
+    int32_t poststream, layout;
     int64_t steps;
 };
 
@@ -207,7 +207,10 @@ LatticeParams lattice_params(const btdf_ctx* ctx) {
         }
     }
     p.nwork = (long long)ctx->cfg.ny * ctx->nseg;
-    for (int a = 0; a < 9; a++) p.poff[a] = (unsigned)(a * ctx->plane);
+    // planar: [9][ny][nxp]; row-interleaved: [ny][9][nxp]
+    p.rs = ctx->cfg.layout == BTDF_LAYOUT_ROWS ? 9u * (unsigned)ctx->nxp : (unsigned)ctx->nxp;
+    for (int a = 0; a < 9; a++)
+        p.poff[a] = ctx->cfg.layout == BTDF_LAYOUT_ROWS ? (unsigned)(a * ctx->nxp) : (unsigned)(a * ctx->plane);
     p.gx = (float)ctx->cfg.gx;
     p.gy = (float)ctx->cfg.gy;
     p.seg_index = ctx->nmark > 0 ? ctx->d_seg_index : nullptr;
@@ -324,8 +327,9 @@ bool encode_tensor_maps(btdf_ctx* ctx) {
                                    : ctx->cfg.storage == kStoreF16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                                                    : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     const cuuint64_t dims[3] = {(cuuint64_t)ctx->nxp, (cuuint64_t)ctx->cfg.ny, 9};
-    const cuuint64_t strides[2] = {(cuuint64_t)ctx->nxp * ctx->elem,
-                                   (cuuint64_t)ctx->plane * ctx->elem};
+    const bool interleaved = ctx->cfg.layout == BTDF_LAYOUT_ROWS;
+    const cuuint64_t strides[2] = {(cuuint64_t)ctx->nxp * ctx->elem * (interleaved ? 9 : 1),
+                                   (cuuint64_t)(interleaved ? ctx->nxp : ctx->plane) * ctx->elem};
     const cuuint32_t estr[3] = {1, 1, 1};
     const int rows[2] = {tma_box_rows(kVarTma8x2), tma_box_rows(kVarTma16x2)};
     for (int b = 0; b < 2; b++)
@@ -476,6 +480,7 @@ int rebuild_markers(btdf_ctx* ctx) {
     if (!csr.empty())
         CK(cudaMemcpyAsync(ctx->d_csr, csr.data(), sizeof(CsrEntry) * csr.size(),
                            cudaMemcpyHostToDevice, st));
+
     CK(cudaMemcpyAsync(ctx->d_body_ptr, body_ptr.data(), sizeof(int) * (nb + 1),
                        cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(ctx->d_body_scale, scale.data(), sizeof(double) * nb,
@@ -521,6 +526,7 @@ int btdf_config_default(btdf_config* cfg) {
     cfg->bc_x = BTDF_BCX_PERIODIC;
     cfg->bc_y = BTDF_BCY_PERIODIC;
     cfg->history_len = 4096;
+    cfg->layout = BTDF_LAYOUT_ROWS;
     return BTDF_OK;
 }
 
@@ -537,6 +543,7 @@ int btdf_create(const btdf_config* cfg, void* stream, btdf_ctx** out) {
     if (c.storage < 0 || c.storage > 2) return BTDF_EINVAL;
     if (c.bc_x < 0 || c.bc_x > 1 || c.bc_y < 0 || c.bc_y > 2) return BTDF_EINVAL;
     if (c.history_len < 1) return BTDF_EINVAL;
+    if (c.layout != BTDF_LAYOUT_PLANES && c.layout != BTDF_LAYOUT_ROWS) return BTDF_EINVAL;
     if (!std::isfinite(c.u_in) || std::fabs(c.u_in) >= 0.5) return BTDF_EINVAL;
     if (!std::isfinite(c.gx) || !std::isfinite(c.gy)) return BTDF_EINVAL;
 
@@ -821,7 +828,7 @@ int btdf_save_state(btdf_ctx* ctx, void* dst, size_t cap, size_t* used) {
     btdf_state_size(ctx, &need);
     if (cap < need) return fail(ctx, BTDF_EINVAL, "destination buffer too small");
     StateHeader h{kStateMagic, ctx->cfg.nx, ctx->cfg.ny, ctx->nxp, ctx->cfg.storage,
-                  ctx->poststream ? 1 : 0, 0, ctx->steps};
+                  ctx->poststream ? 1 : 0, ctx->cfg.layout, ctx->steps};
     std::memcpy(dst, &h, sizeof(h));
     CK(cudaMemcpyAsync((char*)dst + sizeof(h), ctx->g[ctx->cur], need - sizeof(h),
                        cudaMemcpyDeviceToHost, ctx->stream));
@@ -838,7 +845,7 @@ int btdf_load_state(btdf_ctx* ctx, const void* src, size_t len) {
     StateHeader h;
     std::memcpy(&h, src, sizeof(h));
     if (h.magic != kStateMagic || h.nx != ctx->cfg.nx || h.ny != ctx->cfg.ny || h.nxp != ctx->nxp ||
-        h.storage != ctx->cfg.storage || h.steps < 0)
+        h.storage != ctx->cfg.storage || h.layout != ctx->cfg.layout || h.steps < 0)
         return fail(ctx, BTDF_EINVAL, "checkpoint does not match this context");
     CK(cudaMemcpyAsync(ctx->g[ctx->cur], (const char*)src + sizeof(h), need - sizeof(h),
                        cudaMemcpyHostToDevice, ctx->stream));

@@ -70,8 +70,9 @@ struct CsrEntry {
 struct LatticeParams {
     int nx, ny, nxp, nseg;
     long long plane;           // elements per population plane (nxp * ny)
+    unsigned rs;               // elements between consecutive rows of one plane
     long long nwork;           // warp row segments of the LBM kernel
-    unsigned poff[9];          // a * plane: element offset of each population plane
+    unsigned poff[9];          // element offset of population plane a (row 0, x 0)
     int bcx, bcy;
     float omega;               // 1 / tau
     float one_m_omega;         // 1 - 1 / tau

@@ -211,7 +211,7 @@ __device__ void pull_raw(const T* __restrict__ g, const LatticeParams& p, int x,
             if (p.bcx == kBcxPeriodic) sx = sx < 0 ? sx + p.nx : sx - p.nx;
             else sx = sx < 0 ? 0 : p.nx - 1;   // only reached for columns the caller overrides
         }
-        f[a] = Io<T>::ld1(g + pa * p.plane + (long long)sy * p.nxp + sx) + add;
+        f[a] = Io<T>::ld1(g + p.poff[pa] + (unsigned)sy * p.rs + (unsigned)sx) + add;
     }
 }
 
@@ -245,15 +245,15 @@ __device__ __forceinline__ void read_node(const T* __restrict__ g, const Lattice
         pull_node<T>(g, p, x, y, f);
     } else {
 #pragma unroll
-        for (int a = 0; a < 9; a++) f[a] = Io<T>::ld1(g + a * p.plane + (long long)y * p.nxp + x);
+        for (int a = 0; a < 9; a++) f[a] = Io<T>::ld1(g + p.poff[a] + (unsigned)y * p.rs + (unsigned)x);
     }
 }
 
 // ---- the fused LBM kernel ----------------------------------------------------
 
 // Force on every body (Eq. 27) from the Lagrangian forces of this step, in
-// FP64, and the step counter.  Run by block 0 of the LBM kernel, which waits
-// for the IB kernel first.
+// FP64, and the step counter.  Run by block 0 of the LBM kernel after its
+// lattice work, once the IB kernel has finished.
 __device__ void body_forces_and_step(const LatticeParams& p) {
     __shared__ unsigned long long s_step;
     if (p.nbody > 0) cudaGridDependencySynchronize();
@@ -296,7 +296,7 @@ template <typename T, int NPL>
 __device__ __forceinline__ void collide_store(float (&f)[9][NPL], T* __restrict__ gout,
                                               const LatticeParams& p, int y, int xw, int x0,
                                               bool live, int seg) {
-    const unsigned rowoff = (unsigned)y * (unsigned)p.nxp + (unsigned)x0;
+    const unsigned rowoff = (unsigned)y * p.rs + (unsigned)x0;
     // Force density on this lane's nodes: node-centric spread (Eq. 15) of the
     // Lagrangian forces over band segments (after the IB kernel has finished),
     // plus the uniform body force.
@@ -407,12 +407,11 @@ __device__ __forceinline__ void collide_store(float (&f)[9][NPL], T* __restrict_
 // element offsets (the lattice holds fewer than 2^32 / 9 nodes).
 template <typename T, bool kPull, int NPL>
 __device__ __forceinline__ void lbm_segment(const T* __restrict__ gin, T* __restrict__ gout,
-                                            const LatticeParams& p, int y, int xw, int lane) {
+                                            const LatticeParams& p, int y, int xw, int lane,
+                                            int seg) {
     const int x0 = xw + NPL * lane;
     const bool live = x0 < p.nxp;
     const bool lane0 = lane == 0, lane31 = lane == 31;
-    const unsigned nxp = (unsigned)p.nxp;
-    const int seg = band_segment(p, y, xw);
 
     float f[9][NPL];
     if (!kPull || (y > 0 && y < p.ny - 1)) {
@@ -420,11 +419,11 @@ __device__ __forceinline__ void lbm_segment(const T* __restrict__ gin, T* __rest
         // known at compile time.  Lanes past the padded row end load a valid
         // vector and never store.
         const int x0c = live ? x0 : p.nxp - NPL;
-        const unsigned rowc = (unsigned)y * nxp + (unsigned)x0c;
+        const unsigned rowc = (unsigned)y * p.rs + (unsigned)x0c;
 #pragma unroll
         for (int a = 0; a < 9; a++) {
             const int dx = kPull ? -ex(a) : 0, dy = kPull ? -ey(a) : 0;
-            const unsigned off = p.poff[a] + rowc + (unsigned)(dy * (int)nxp);
+            const unsigned off = p.poff[a] + rowc + (unsigned)(dy * (int)p.rs);
             Io<T>::template ldv<NPL>(gin + off, f[a]);
             float edge = 0.0f;
             if (dx < 0 && lane0 && x0 > 0) edge = Io<T>::ld1(gin + (off - 1));
@@ -444,7 +443,7 @@ __device__ __forceinline__ void lbm_segment(const T* __restrict__ gin, T* __rest
             }
         }
     } else {
-    const unsigned rowoff = (unsigned)y * nxp + (unsigned)x0;
+    const unsigned rowoff = (unsigned)y * p.rs + (unsigned)x0;
     float edge[9];
     int shift[9];
 #pragma unroll
@@ -458,7 +457,7 @@ __device__ __forceinline__ void lbm_segment(const T* __restrict__ gin, T* __rest
                 float unused;
                 y_source(a, y, p, pa, sy, dx, unused);
             }
-            off = p.poff[pa] + (unsigned)sy * nxp + (unsigned)x0;
+            off = p.poff[pa] + (unsigned)sy * p.rs + (unsigned)x0;
         } else {
             off = p.poff[a] + rowoff;
         }
@@ -523,16 +522,20 @@ __device__ __forceinline__ void lbm_segment(const T* __restrict__ gin, T* __rest
 template <typename T, bool kPull, int NPL, int MINB>
 __global__ void __launch_bounds__(kThreads, MINB)
 collide_stream_kernel(const T* __restrict__ gin, T* __restrict__ gout, LatticeParams p) {
-    if (blockIdx.x == 0) body_forces_and_step(p);
     constexpr int SW = 32 * NPL;
     const int lane = threadIdx.x & 31;
     const int nsegw = (p.nxp + SW - 1) / SW;
     const int nw = gridDim.x * (blockDim.x >> 5);
     const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int y = w0 / nsegw, s = w0 - y * nsegw;
+    const int y0 = w0 / nsegw, s0 = w0 - y0 * nsegw;
     const int dy = nw / nsegw, ds = nw - dy * nsegw;
+    // Band segments wait for the IB kernel's forces inside lbm_segment; the
+    // body-force reduction comes after block 0's lattice work, when the IB
+    // kernel has long finished.
+    int y = y0, s = s0;
     while (y < p.ny) {
-        lbm_segment<T, kPull, NPL>(gin, gout, p, y, s * SW, lane);
+        const int seg = band_segment(p, y, s * SW);
+        lbm_segment<T, kPull, NPL>(gin, gout, p, y, s * SW, lane, seg);
         s += ds;
         y += dy;
         if (s >= nsegw) {
@@ -540,6 +543,7 @@ collide_stream_kernel(const T* __restrict__ gin, T* __restrict__ gout, LatticePa
             y += 1;
         }
     }
+    if (blockIdx.x == 0) body_forces_and_step(p);
 }
 
 // ---- the software-pipelined LBM kernel ------------------------------------------
@@ -557,12 +561,11 @@ __device__ __forceinline__ void issue_interior(const T* __restrict__ gin, const 
                                                int xw, int lane, RawSeg<NPL>& r) {
     const int x0 = xw + NPL * lane;
     const int x0c = x0 < p.nxp ? x0 : p.nxp - NPL;
-    const unsigned nxp = (unsigned)p.nxp;
-    const unsigned rowc = (unsigned)y * nxp + (unsigned)x0c;
+    const unsigned rowc = (unsigned)y * p.rs + (unsigned)x0c;
 #pragma unroll
     for (int a = 0; a < 9; a++) {
         const int dx = -ex(a), dy = -ey(a);
-        const unsigned off = p.poff[a] + rowc + (unsigned)(dy * (int)nxp);
+        const unsigned off = p.poff[a] + rowc + (unsigned)(dy * (int)p.rs);
         Io<T>::template ldv<NPL>(gin + off, r.v[a]);
         r.e[a] = 0.0f;
         if (dx < 0 && lane == 0 && x0 > 0) r.e[a] = Io<T>::ld1(gin + (off - 1));
@@ -599,7 +602,6 @@ __device__ __forceinline__ void shift_interior(RawSeg<NPL>& r, int lane, float (
 template <typename T, int NPL>
 __global__ void __launch_bounds__(kThreads, 2)
 collide_stream_pf_kernel(const T* __restrict__ gin, T* __restrict__ gout, LatticeParams p) {
-    if (blockIdx.x == 0) body_forces_and_step(p);
     constexpr int SW = 32 * NPL;
     const int lane = threadIdx.x & 31;
     const int nsegw = (p.nxp + SW - 1) / SW;
@@ -640,13 +642,14 @@ collide_stream_pf_kernel(const T* __restrict__ gin, T* __restrict__ gout, Lattic
             }
             collide_store<T, NPL>(f, gout, p, y, xw, x0, live, seg);
         } else {
-            lbm_segment<T, true, NPL>(gin, gout, p, y, xw, lane);
+            lbm_segment<T, true, NPL>(gin, gout, p, y, xw, lane, band_segment(p, y, xw));
         }
         cur = nxt;
         y = yn;
         s = sn;
         interior = n_interior;
     }
+    if (blockIdx.x == 0) body_forces_and_step(p);
 }
 
 // ---- the TMA-tiled LBM kernel ---------------------------------------------------
@@ -734,8 +737,6 @@ collide_stream_tma_kernel(const __grid_constant__ CUtensorMap tmap, const T* __r
     unsigned long long* bars = (unsigned long long*)(stages + S * C::STAGE_STRIDE);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    if (blockIdx.x == 0) body_forces_and_step(p);
-
     const int ntx = (p.nxp + C::TW - 1) / C::TW;
     const int ntiles = ntx * ((p.ny + TH - 1) / TH);
     if (tid == 0) {
@@ -815,7 +816,7 @@ collide_stream_tma_kernel(const __grid_constant__ CUtensorMap tmap, const T* __r
                         v[0] = v[1]; v[1] = v[2]; v[2] = v[3]; v[3] = next;
                     }
                 } else {                                    // periodic wrap row: global
-                    const T* grow = gin + p.poff[pa] + (unsigned)sy * (unsigned)p.nxp;
+                    const T* grow = gin + p.poff[pa] + (unsigned)sy * p.rs;
                     if (live) Io<T>::template ldv<4>(grow + x0, v);
                     else v[0] = v[1] = v[2] = v[3] = 0.0f;
                     if (dx < 0) {
@@ -868,6 +869,7 @@ collide_stream_tma_kernel(const __grid_constant__ CUtensorMap tmap, const T* __r
             }
         }
     }
+    if (blockIdx.x == 0) body_forces_and_step(p);
 }
 
 // ---- the IB stage -------------------------------------------------------------
@@ -973,7 +975,7 @@ __global__ void init_kernel(T* g, LatticeParams p, const double* rho, const doub
         const double pU = 3.0 * eU + 4.5 * eU * eU - 1.5 * (Ux * Ux + Uy * Uy);
         // f_eq(rho, u) - f_eq(1, U_r) = w [(rho - 1)(1 + P(u)) + P(u) - P(U_r)], Eq. 6
         const double dev = w * ((r - 1.0) * (1.0 + pu) + (pu - pU));
-        store_scalar<T>(g + a * p.plane + (long long)y * p.nxp + x, (float)dev);
+        store_scalar<T>(g + p.poff[a] + (unsigned)y * p.rs + (unsigned)x, (float)dev);
     }
 }
 

@@ -33,8 +33,8 @@ def test_every_declared_symbol_is_exported():
 
 
 def test_config_struct_size_matches():
-    # 2 int32 + 2 double + 6 int32 + 2 double, no padding holes
-    assert ctypes.sizeof(B.btdf_config) == 64
+    # 2 int32 + 2 double + 6 int32 + 2 double + 2 int32, no padding holes
+    assert ctypes.sizeof(B.btdf_config) == 72
 
 
 def test_version_and_status_strings():
@@ -46,7 +46,7 @@ def test_version_and_status_strings():
 @pytest.mark.parametrize("field,value", [
     ("tau", 0.5), ("tau", float("nan")), ("nx", 3), ("ny", 0), ("delta", 1), ("delta", 6),
     ("nf", 0), ("nf", 65), ("storage", 3), ("bc_x", 2), ("bc_y", 3), ("history_len", 0),
-    ("u_in", float("inf")), ("u_in", 0.6), ("gx", float("nan")),
+    ("u_in", float("inf")), ("u_in", 0.6), ("gx", float("nan")), ("layout", 2),
 ])
 def test_invalid_config_rejected_on_host(field, value):
     cfg = B.btdf_config_default()

@@ -269,17 +269,19 @@ VARIANTS = [(1, 0), (2, 0), (3, 0), (4, 0), (5, 0), (6, 0), (7, 0), (1, 7), (2, 
 
 @pytest.mark.parametrize("storage", [B.BTDF_F32, B.BTDF_F16DEV, B.BTDF_BF16DEV])
 def test_kernel_variants_agree_bitwise(storage):
-    """Register-pipelined and TMA-tiled kernels, and any grid size, change the
-    schedule, not the arithmetic: all give bitwise identical results."""
+    """Register-pipelined and TMA-tiled kernels, any grid size and either
+    population layout change the schedule, not the arithmetic: all give
+    bitwise identical results."""
     case = W.small_cylinder(delta=3, seed=13)
     case.nx, case.ny = 300, 70          # several tiles, a ragged last tile
     case.bodies = [W.circle_markers(80.3, 35.2, 16.0, 50)]
     outs = []
-    for variant, grid in VARIANTS:
-        lat = B.Lattice.from_case(case, storage=storage)
-        lat.tune(variant, grid)
-        lat.step(150)
-        outs.append((lat.field(B.FIELD_UX), lat.field(B.FIELD_UY), lat.forces(0)[0]))
+    for layout in (B.LAYOUT_ROWS, B.LAYOUT_PLANES):
+        for variant, grid in VARIANTS:
+            lat = B.Lattice.from_case(case, storage=storage, layout=layout)
+            lat.tune(variant, grid)
+            lat.step(150)
+            outs.append((lat.field(B.FIELD_UX), lat.field(B.FIELD_UY), lat.forces(0)[0]))
     for o in outs[1:]:
         for a, b in zip(outs[0], o):
             assert np.array_equal(a, b)
