@@ -202,6 +202,50 @@ int btdf_tune(btdf_ctx *ctx, int32_t variant, int32_t grid_blocks);
 /* Bytes of device memory the context holds. */
 int btdf_device_bytes(const btdf_ctx *ctx, size_t *bytes);
 
+/* ---- IB force stage without device allocation ----------------------------
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot call cudaMalloc: code that runs inside another framework's memory
+ * budget (a caching allocator owns the device memory), code issued while a
+ * CUDA stream is being captured into a graph (allocation is not permitted
+ * there), or real-time loops that must not enter the driver's allocator.
+ *
+ * For one body of n markers it runs the IB stage of one step on a population
+ * buffer the caller owns: interpolation of rho and u* to the markers
+ * (Eqs. 9-10, 12, 14), the force F_b = 2 rho_l (U_b - D_I u*) (Eq. 20) and
+ * the force on the body F_p = -sum F_b ds drs in FP64 (Eq. 27).  It uses the
+ * same kernel as btdf_step's IB stage.
+ *   cfg    lattice description (nx, ny, u_in, delta, storage, bc_x, bc_y,
+ *          layout; tau, nf, history_len and g are not used).
+ *   pops   device pointer to populations in the library's layout: the
+ *          storage type, deviations f_a - f_eq_a(1, (u_in, 0)), rows of
+ *          nxp = nx rounded up to 32, planar or row-interleaved per
+ *          cfg->layout.  This is the byte image btdf_save_state writes after
+ *          its 40-byte header.
+ *   pull   0: pops holds post-streaming populations; 1: post-collision ones
+ *          (streaming and the boundary rules are applied while reading).  A
+ *          checkpoint's header says which (its int32 at byte 24 is 1 for
+ *          post-streaming).
+ *   X, Y, Ubx, Uby, ds, drs  as in btdf_add_markers (host arrays of n
+ *          doubles; Ubx/Uby may be NULL; drs <= 0 takes Sec. 4.4's value).
+ *   Fb     device output, 2n floats (F_b per marker, x and y interleaved).
+ *   Fp     host output, 2 doubles (force on the body).
+ *   stream cudaStream_t to run on (NULL = legacy default stream); the call
+ *          synchronizes it before returning.
+ * No device memory is allocated: the marker tables and the reduction scratch
+ * live in one file-scope device array of about 320 KB, which every GPU that
+ * loads the library holds until the process exits.  n may not exceed
+ * BTDF_STATIC_MAX_MARKERS (EINVAL).  The first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  Every call reuses the same array, so calls that
+ * overlap on the GPU (two streams, two host threads) race: serialize them.
+ * Errors: EINVAL (arguments, n out of range), ECUDA, EUNSTABLE (density or
+ * force at a marker non-positive or non-finite). */
+#define BTDF_STATIC_MAX_MARKERS 2048
+int btdf_ib_forces_static(const btdf_config *cfg, const void *pops, int32_t pull, int32_t n,
+                          const double *X, const double *Y, const double *Ubx,
+                          const double *Uby, double ds, double drs, float *Fb, double *Fp,
+                          void *stream);
+
 const char *btdf_last_error(const btdf_ctx *ctx);
 const char *btdf_status_string(int status);
 int btdf_version(void);

@@ -32,8 +32,10 @@ EXPORTS = [
     "btdf_read_forces", "btdf_read_markers", "btdf_read_field", "btdf_step_count",
     "btdf_state_size", "btdf_save_state", "btdf_load_state", "btdf_profile_enable",
     "btdf_profile_read", "btdf_tune", "btdf_device_bytes", "btdf_last_error", "btdf_status_string",
-    "btdf_version",
+    "btdf_version", "btdf_ib_forces_static",
 ]
+STATIC_MAX_MARKERS = 2048
+STATE_HEADER_BYTES = 40
 
 
 class btdf_config(C.Structure):
@@ -99,6 +101,8 @@ def lib() -> C.CDLL:
     L.btdf_status_string.argtypes = [C.c_int]
     L.btdf_status_string.restype = C.c_char_p
     L.btdf_version.restype = C.c_int
+    L.btdf_ib_forces_static.argtypes = [C.POINTER(btdf_config), vp, C.c_int32, C.c_int32, _dp, _dp,
+                                        vp, vp, C.c_double, C.c_double, vp, _dp, vp]
     _lib = L
     return L
 
@@ -123,6 +127,24 @@ def btdf_status_string(rc: int) -> str:
 
 def btdf_version() -> int:
     return lib().btdf_version()
+
+
+def btdf_ib_forces_static(cfg: btdf_config, pops_ptr: int, pull: bool, X, Y, ds, Ubx=None,
+                          Uby=None, drs=0.0, fb_ptr: int = 0, stream: int = 0):
+    """IB force stage of one body on a caller-owned device population buffer,
+    without any device allocation (see include/btdf.h).  Returns
+    (status, (Fx, Fy)); F_b per marker is written to the device pointer fb_ptr."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    Y = np.ascontiguousarray(Y, dtype=np.float64)
+    ubx = None if Ubx is None else np.ascontiguousarray(Ubx, dtype=np.float64)
+    uby = None if Uby is None else np.ascontiguousarray(Uby, dtype=np.float64)
+    Fp = np.zeros(2)
+    rc = lib().btdf_ib_forces_static(C.byref(cfg), C.c_void_p(pops_ptr), 1 if pull else 0, len(X),
+                                     X, Y, None if ubx is None else ubx.ctypes.data,
+                                     None if uby is None else uby.ctypes.data, float(ds),
+                                     float(drs or 0.0), C.c_void_p(fb_ptr), Fp,
+                                     C.c_void_p(stream or None))
+    return rc, (float(Fp[0]), float(Fp[1]))
 
 
 def _f64(a) -> np.ndarray:
