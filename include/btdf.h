@@ -202,6 +202,45 @@ int btdf_tune(btdf_ctx *ctx, int32_t variant, int32_t grid_blocks);
 /* Bytes of device memory the context holds. */
 int btdf_device_bytes(const btdf_ctx *ctx, size_t *bytes);
 
+/* ---- batched form --------------------------------------------------------
+ * Many independent lattices (each with its own size, relaxation time,
+ * inflow, boundary kinds and bodies) advanced together: one IB launch over
+ * the markers of all lattices and one persistent collide-stream launch over
+ * all lattices per step, replayed through CUDA graphs.  Each lattice computes
+ * exactly what a single context with the same configuration computes.  All
+ * lattices share storage, layout, delta function, history_len and nf = 1.
+ * Fields and markers are set before the first step.  Body ids count bodies in
+ * the order they were added, over all lattices. */
+typedef struct btdf_batch btdf_batch;
+
+/* cfgs: n configurations.  Errors: EINVAL (a bad configuration or mixed
+ * storage / layout / delta / history_len, nf != 1), ENOMEM, ECUDA. */
+int btdf_batch_create(const btdf_config *cfgs, int32_t n, void *stream, btdf_batch **out);
+int btdf_batch_destroy(btdf_batch *b);
+/* As btdf_init_fields, for lattice `lattice`. */
+int btdf_batch_init_fields(btdf_batch *b, int32_t lattice, const double *rho, const double *ux,
+                           const double *uy);
+/* As btdf_add_markers, for lattice `lattice`; *body_id receives the batch-wide
+ * body id. */
+int btdf_batch_add_markers(btdf_batch *b, int32_t lattice, int32_t n, const double *X,
+                           const double *Y, const double *Ubx, const double *Uby, double ds,
+                           double drs, int32_t *body_id);
+int btdf_batch_body_count(const btdf_batch *b, int32_t *n);
+int btdf_batch_body_lattice(const btdf_batch *b, int32_t body, int32_t *lattice);
+/* Collide-stream launch shape: 1 = 4 nodes per lane, 2 = 2 nodes per lane,
+ * 0 = default (1).  Results do not depend on it. */
+int btdf_batch_tune(btdf_batch *b, int32_t variant);
+int btdf_batch_step(btdf_batch *b, int64_t nsteps);
+int btdf_batch_sync(btdf_batch *b);
+int64_t btdf_batch_step_count(const btdf_batch *b);
+/* As btdf_read_forces, for a batch-wide body id. */
+int btdf_batch_read_forces(btdf_batch *b, int32_t body, int64_t first, int64_t n, double *Fx,
+                           double *Fy);
+/* As btdf_read_field, for lattice `lattice`. */
+int btdf_batch_read_field(btdf_batch *b, int32_t lattice, int32_t kind, float *dst,
+                          int32_t dst_is_device);
+const char *btdf_batch_last_error(const btdf_batch *b);
+
 /* ---- IB force stage without device allocation ----------------------------
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot call cudaMalloc: code that runs inside another framework's memory

@@ -33,6 +33,10 @@ EXPORTS = [
     "btdf_state_size", "btdf_save_state", "btdf_load_state", "btdf_profile_enable",
     "btdf_profile_read", "btdf_tune", "btdf_device_bytes", "btdf_last_error", "btdf_status_string",
     "btdf_version", "btdf_ib_forces_static",
+    "btdf_batch_create", "btdf_batch_destroy", "btdf_batch_init_fields", "btdf_batch_add_markers",
+    "btdf_batch_body_count", "btdf_batch_body_lattice", "btdf_batch_tune", "btdf_batch_step",
+    "btdf_batch_sync", "btdf_batch_step_count", "btdf_batch_read_forces", "btdf_batch_read_field",
+    "btdf_batch_last_error",
 ]
 STATIC_MAX_MARKERS = 2048
 STATE_HEADER_BYTES = 40
@@ -103,6 +107,22 @@ def lib() -> C.CDLL:
     L.btdf_version.restype = C.c_int
     L.btdf_ib_forces_static.argtypes = [C.POINTER(btdf_config), vp, C.c_int32, C.c_int32, _dp, _dp,
                                         vp, vp, C.c_double, C.c_double, vp, _dp, vp]
+    L.btdf_batch_create.argtypes = [C.POINTER(btdf_config), C.c_int32, vp, C.POINTER(vp)]
+    L.btdf_batch_destroy.argtypes = [vp]
+    L.btdf_batch_init_fields.argtypes = [vp, C.c_int32, _dp, _dp, _dp]
+    L.btdf_batch_add_markers.argtypes = [vp, C.c_int32, C.c_int32, _dp, _dp, vp, vp, C.c_double,
+                                         C.c_double, C.POINTER(C.c_int32)]
+    L.btdf_batch_body_count.argtypes = [vp, C.POINTER(C.c_int32)]
+    L.btdf_batch_body_lattice.argtypes = [vp, C.c_int32, C.POINTER(C.c_int32)]
+    L.btdf_batch_tune.argtypes = [vp, C.c_int32]
+    L.btdf_batch_step.argtypes = [vp, C.c_int64]
+    L.btdf_batch_sync.argtypes = [vp]
+    L.btdf_batch_step_count.argtypes = [vp]
+    L.btdf_batch_step_count.restype = C.c_int64
+    L.btdf_batch_read_forces.argtypes = [vp, C.c_int32, C.c_int64, C.c_int64, vp, vp]
+    L.btdf_batch_read_field.argtypes = [vp, C.c_int32, C.c_int32, vp, C.c_int32]
+    L.btdf_batch_last_error.argtypes = [vp]
+    L.btdf_batch_last_error.restype = C.c_char_p
     _lib = L
     return L
 
@@ -288,3 +308,100 @@ class Lattice:
         n = C.c_size_t()
         self._check(lib().btdf_device_bytes(self._ctx, C.byref(n)), "btdf_device_bytes")
         return n.value
+
+
+def _case_config(case, storage=BTDF_F32, history_len=4096, layout=None) -> btdf_config:
+    cfg = btdf_config_default()
+    cfg.nx, cfg.ny, cfg.tau, cfg.u_in = case.nx, case.ny, float(case.tau), float(case.u_in)
+    cfg.delta, cfg.nf, cfg.storage = int(case.delta), int(case.nf), int(storage)
+    cfg.bc_x, cfg.bc_y, cfg.history_len = int(case.bc_x), int(case.bc_y), int(history_len)
+    cfg.gx, cfg.gy = float(case.gx), float(case.gy)
+    if layout is not None:
+        cfg.layout = int(layout)
+    return cfg
+
+
+class Batch:
+    """Many independent lattices advanced together (btdf_batch_*)."""
+
+    def __init__(self, cases, storage=BTDF_F32, history_len=4096, stream: int = 0, layout=None):
+        n = len(cases)
+        cfgs = (btdf_config * n)(*[_case_config(c, storage, history_len, layout) for c in cases])
+        out = C.c_void_p()
+        rc = lib().btdf_batch_create(cfgs, n, C.c_void_p(stream or None), C.byref(out))
+        if rc != BTDF_OK:
+            raise BtdfError(rc, f"btdf_batch_create: {btdf_status_string(rc)}")
+        self._b = out.value
+        self.cases = list(cases)
+        self.bodies = []          # (lattice, markers) per batch-wide body id
+
+    @classmethod
+    def from_cases(cls, cases, storage=BTDF_F32, history_len=4096, stream: int = 0, layout=None):
+        bt = cls(cases, storage, history_len, stream, layout)
+        for i, c in enumerate(cases):
+            bt.init_fields(i, *c.initial_fields())
+        for i, c in enumerate(cases):
+            for b in c.bodies:
+                bt.add_markers(i, b.X, b.Y, b.ds, b.Ubx, b.Uby, drs=c.drs)
+        return bt
+
+    def _check(self, rc, what):
+        if rc != BTDF_OK:
+            msg = lib().btdf_batch_last_error(self._b).decode()
+            raise BtdfError(rc, f"{what}: {btdf_status_string(rc)}: {msg}")
+
+    def close(self):
+        if getattr(self, "_b", None):
+            lib().btdf_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_fields(self, lattice, rho, ux, uy):
+        self._check(lib().btdf_batch_init_fields(self._b, lattice, _f64(rho), _f64(ux), _f64(uy)),
+                    "btdf_batch_init_fields")
+
+    def add_markers(self, lattice, X, Y, ds, Ubx=None, Uby=None, drs=0.0) -> int:
+        X, Y = _f64(X), _f64(Y)
+        ubx = None if Ubx is None else _f64(Ubx)
+        uby = None if Uby is None else _f64(Uby)
+        bid = C.c_int32(-1)
+        rc = lib().btdf_batch_add_markers(self._b, lattice, len(X), X, Y,
+                                          None if ubx is None else ubx.ctypes.data,
+                                          None if uby is None else uby.ctypes.data, float(ds),
+                                          float(drs or 0.0), C.byref(bid))
+        self._check(rc, "btdf_batch_add_markers")
+        self.bodies.append((lattice, len(X)))
+        return bid.value
+
+    def tune(self, variant):
+        self._check(lib().btdf_batch_tune(self._b, int(variant)), "btdf_batch_tune")
+
+    def step(self, n=1):
+        self._check(lib().btdf_batch_step(self._b, int(n)), "btdf_batch_step")
+
+    def sync(self):
+        self._check(lib().btdf_batch_sync(self._b), "btdf_batch_sync")
+
+    @property
+    def steps(self):
+        return lib().btdf_batch_step_count(self._b)
+
+    def forces(self, body, first=0, n=None):
+        n = self.steps - first if n is None else n
+        Fx, Fy = np.zeros(n), np.zeros(n)
+        self._check(lib().btdf_batch_read_forces(self._b, body, first, n, Fx.ctypes.data,
+                                                 Fy.ctypes.data), "btdf_batch_read_forces")
+        return Fx, Fy
+
+    def field(self, lattice, kind):
+        c = self.cases[lattice]
+        shape = (9, c.ny, c.nx) if kind == FIELD_POPS else (c.ny, c.nx)
+        out = np.zeros(shape, dtype=np.float32)
+        self._check(lib().btdf_batch_read_field(self._b, lattice, kind, out.ctypes.data, 0),
+                    "btdf_batch_read_field")
+        return out

@@ -38,27 +38,6 @@ struct StateHeader {
     int64_t steps;
 };
 
-// Regularized delta functions of Sec. 4.3 evaluated in FP64 on the host.
-double delta_fn(int kind, double r) {
-    const double a = std::fabs(r);
-    switch (kind) {
-    case 2:  // Eq. 37
-        return a <= 1.0 ? 1.0 - a : 0.0;
-    case 3:  // Eq. 38
-        if (a > 1.5) return 0.0;
-        if (a > 0.5) return (5.0 - 3.0 * a - std::sqrt(1.0 - 3.0 * (1.0 - a) * (1.0 - a))) / 6.0;
-        return (1.0 + std::sqrt(1.0 - 3.0 * a * a)) / 3.0;
-    case 4:  // Eq. 39
-        if (a >= 2.0) return 0.0;
-        if (a >= 1.0) return (5.0 - 2.0 * a - std::sqrt(-7.0 + 12.0 * a - 4.0 * a * a)) / 8.0;
-        return (3.0 - 2.0 * a + std::sqrt(1.0 + 4.0 * a - 4.0 * a * a)) / 8.0;
-    case 5:  // cosine kernel with 4-point support
-        return a < 2.0 ? 0.25 * (1.0 + std::cos(M_PI * a * 0.5)) : 0.0;
-    default:
-        return 0.0;
-    }
-}
-
 int support_width(int kind) { return kind == 2 ? 2 : kind == 3 ? 3 : (kind == 4 || kind == 5) ? 4 : 0; }
 
 // Solid-shell thickness drs/dh suggested in Sec. 4.4 (the cosine kernel has
@@ -359,97 +338,35 @@ int read_status(btdf_ctx* ctx) {
 int rebuild_markers(btdf_ctx* ctx) {
     drop_graphs(ctx);
     free_markers(ctx);
-    const int nx = ctx->cfg.nx, ny = ctx->cfg.ny, S = ctx->width;
+    const int nx = ctx->cfg.nx, ny = ctx->cfg.ny;
     const bool px = ctx->cfg.bc_x == kBcxPeriodic, py = ctx->cfg.bc_y == kBcyPeriodic;
     const int nm = ctx->nmark, nb = (int)ctx->bodies.size();
+    (void)nx;
     if (nm == 0) return BTDF_OK;
-    std::vector<Marker> mk(nm);
-    struct Ent { long long node; int marker; double w; };
-    std::vector<Ent> ents;
-    ents.reserve((size_t)nm * S * S);
+    std::vector<BodyDesc> descs;
     std::vector<int> body_ptr(nb + 1);
     std::vector<double> scale(nb);
-    ctx->aux_host.assign(nm, MarkerAux{});
     for (int b = 0; b < nb; b++) {
-        Body& B = ctx->bodies[b];
-        B.wsum.assign(B.n, 0.0);
+        const Body& B = ctx->bodies[b];
+        descs.push_back(BodyDesc{B.n, B.ds, B.drs, B.X.data(), B.Y.data(), B.Ubx.data(),
+                                 B.Uby.data(), b});
         body_ptr[b] = B.first;
         body_ptr[b + 1] = B.first + B.n;
         scale[b] = B.ds * B.drs;
-        for (int l = 0; l < B.n; l++) {
-            const int m = B.first + l;
-            const double X = B.X[l], Y = B.Y[l];
-            const int i0 = (int)std::floor(X - 0.5 * S) + 1;   // first node with x > X - S/2
-            const int j0 = (int)std::floor(Y - 0.5 * S) + 1;
-            double wx[4] = {0, 0, 0, 0}, wy[4] = {0, 0, 0, 0};
-            bool okx[4] = {false, false, false, false}, oky[4] = {false, false, false, false};
-            Marker& M = mk[m];
-            for (int i = 0; i < 4; i++) {
-                M.xs[i] = 0;
-                M.ys[i] = 0;
-            }
-            for (int i = 0; i < S; i++) {
-                int x = i0 + i, y = j0 + i;
-                wx[i] = delta_fn(ctx->cfg.delta, (double)x - X);
-                wy[i] = delta_fn(ctx->cfg.delta, (double)y - Y);
-                if (px) x = ((x % nx) + nx) % nx;
-                if (py) y = ((y % ny) + ny) % ny;
-                okx[i] = x >= 0 && x < nx;
-                oky[i] = y >= 0 && y < ny;
-                M.xs[i] = std::min(std::max(x, 0), nx - 1);
-                M.ys[i] = std::min(std::max(y, 0), ny - 1);
-            }
-            for (int k = 0; k < 16; k++) M.w[k] = 0.0f;
-            for (int j = 0; j < S; j++)
-                for (int i = 0; i < S; i++) {
-                    if (!okx[i] || !oky[j]) continue;
-                    const double w = wx[i] * wy[j];
-                    M.w[j * S + i] = (float)w;
-                    B.wsum[l] += w;
-                    if (w != 0.0)
-                        ents.push_back({(long long)M.ys[j] * nx + M.xs[i], m, w * B.drs * B.ds});
-                }
-            MarkerAux& A = ctx->aux_host[m];
-            A.wsum = (float)B.wsum[l];
-            A.ubx_rel = (float)(B.Ubx[l] - ctx->cfg.u_in * B.wsum[l]);
-            A.uby_rel = (float)B.Uby[l];
-            A.body = b;
-        }
     }
-    std::sort(ents.begin(), ents.end(), [](const Ent& a, const Ent& b) {
-        return a.node != b.node ? a.node < b.node : a.marker < b.marker;
-    });
-    // Band segments: 128-node runs of a row holding at least one band node.
-    std::vector<int> seg_index((size_t)ny * ctx->nseg, -1);
-    std::vector<long long> seg_keys;
-    for (const Ent& e : ents) {
-        const long long y = e.node / nx, x = e.node % nx;
-        const long long key = y * ctx->nseg + x / kSeg;
-        if (seg_keys.empty() || seg_keys.back() != key) seg_keys.push_back(key);
+    HostTables t;
+    build_marker_tables(ctx->cfg.nx, ctx->cfg.ny, ctx->nseg, ctx->cfg.delta, ctx->width, px, py,
+                        ctx->cfg.u_in, descs, 0, t);
+    for (int b = 0; b < nb; b++) {
+        Body& B = ctx->bodies[b];
+        B.wsum.assign(t.wsum.begin() + B.first, t.wsum.begin() + B.first + B.n);
     }
-    ctx->nband = (int)seg_keys.size();
-    for (int s = 0; s < ctx->nband; s++) seg_index[seg_keys[s]] = s;
-    std::vector<int> seg_ptr((size_t)ctx->nband * (kSeg + 1), 0);
-    std::vector<CsrEntry> csr(ents.size());
-    {
-        // entries are sorted by node, so each segment's entries are contiguous
-        size_t k = 0;
-        for (int s = 0; s < ctx->nband; s++) {
-            const long long key = seg_keys[s];
-            const long long y = key / ctx->nseg, xs0 = (key % ctx->nseg) * kSeg;
-            int* ptr = &seg_ptr[(size_t)s * (kSeg + 1)];
-            for (int i = 0; i < kSeg; i++) {
-                ptr[i] = (int)k;
-                const long long node = y * nx + xs0 + i;
-                while (k < ents.size() && ents[k].node == node && xs0 + i < nx) {
-                    csr[k].marker = ents[k].marker;
-                    csr[k].w = (float)ents[k].w;
-                    k++;
-                }
-            }
-            ptr[kSeg] = (int)k;
-        }
-    }
+    ctx->aux_host = t.aux;
+    ctx->nband = (int)t.seg_keys.size();
+    const std::vector<Marker>& mk = t.mk;
+    const std::vector<int>& seg_index = t.seg_index;
+    const std::vector<int>& seg_ptr = t.seg_ptr;
+    const std::vector<CsrEntry>& csr = t.csr;
     const size_t nseg_all = (size_t)ny * ctx->nseg;
     const size_t bytes_before = ctx->dev_bytes;
     CK(dalloc(ctx, &ctx->d_mk, sizeof(Marker) * nm));

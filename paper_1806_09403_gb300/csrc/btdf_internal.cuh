@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
@@ -114,6 +115,22 @@ struct IbParams {
 
 enum : int { kStatusUnstable = 1, kStatusTimeout = 2 };
 
+// Batched LBM launch: many lattices, one persistent grid.
+struct BatchLbm {
+    const LatticeParams* descs;             // per lattice
+    const unsigned long long* case_off;     // element offset of each lattice's populations
+    const int2* units;                      // (lattice, first row) of each 8-row block
+    const int* cta_units;                   // [grid + 1] first unit of each CTA
+    int nbody;
+    int hist_len;
+    const int* body_rng;                    // [2 * nbody] first and end flat marker index
+    const double* body_scale;               // ds * drs per body
+    double2* hist;                          // [hist_len * nbody]
+    const float2* F;                        // Lagrangian forces of the step
+    unsigned long long* step;               // step counter, advanced by the last CTA
+    unsigned int* done;                     // CTAs finished this launch, reset by the last
+};
+
 // Launchers implemented in btdf_kernels.cu.
 // npl: nodes per lane (4 or 2; -4 / -2: software-pipelined kernel, pull
 // steps only); grid: upper bound on the blocks of the
@@ -142,6 +159,12 @@ cudaError_t launch_collide_stream_tma(int storage, int variant, const CUtensorMa
                                       void* gout, const LatticeParams& p, int grid, bool pdl,
                                       cudaStream_t st);
 int collide_stream_tma_blocks_per_sm(int storage, int variant);
+cudaError_t launch_collide_stream_batch(int storage, bool pull, int npl, const void* gin, void* gout,
+                                        const BatchLbm& b, int grid, bool pdl, cudaStream_t st);
+int collide_stream_batch_blocks_per_sm(int storage, int npl);
+cudaError_t launch_ib_force_batch(int storage, bool pull, int width, const void* g,
+                                  const LatticeParams* descs, const unsigned long long* case_off,
+                                  const IbParams& q, cudaStream_t st);
 int tma_box_rows(int variant);
 int tma_halo(int storage);
 cudaError_t launch_ib_force(int storage, bool pull, int width, const void* g,
@@ -151,5 +174,30 @@ cudaError_t launch_init_equilibrium(int storage, void* g, const LatticeParams& p
                                     cudaStream_t st);
 cudaError_t launch_read_field(int storage, bool pull, const void* g, const LatticeParams& p,
                               int kind, float* dst, cudaStream_t st);
+
+// ---- host-side static tables (btdf_tables.cu) ----
+
+// One rigid body as seen by the table builder; tag goes to MarkerAux.body.
+struct BodyDesc {
+    int n;
+    double ds, drs;
+    const double *X, *Y, *Ubx, *Uby;   // velocities may be null (at rest)
+    int tag;
+};
+
+struct HostTables {
+    std::vector<Marker> mk;
+    std::vector<MarkerAux> aux;
+    std::vector<double> wsum;          // FP64 sum of each marker's weights
+    std::vector<int> seg_index;        // [ny * nseg]
+    std::vector<long long> seg_keys;   // y * nseg + segment, ascending
+    std::vector<int> seg_ptr;          // [nband * (kSeg + 1)]
+    std::vector<CsrEntry> csr;         // marker indices offset by marker_base
+};
+
+double delta_fn(int kind, double r);
+void build_marker_tables(int nx, int ny, int nseg, int delta, int width, bool px, bool py,
+                         double u_in, const std::vector<BodyDesc>& bodies, int marker_base,
+                         HostTables& t);
 
 }  // namespace btdf

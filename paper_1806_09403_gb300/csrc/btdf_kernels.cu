@@ -61,11 +61,18 @@ template <typename H, typename H2> struct Io16 {
     static __device__ __forceinline__ float2 to2(unsigned u);
     static __device__ __forceinline__ unsigned from2(float a, float b);
 };
+// FP16 stores the deviations scaled by 2^10: the bulk of the lattice sits
+// 1e-6 .. 1e-3 away from the reference equilibrium, where unscaled FP16 would
+// be subnormal; the largest deviations (~0.1 near a body at start-up) stay far
+// below FP16's range after scaling.  Power-of-two scaling is exact.
+constexpr float kHalfScale = 1024.0f;
+constexpr float kHalfInvScale = 1.0f / 1024.0f;
 template <> __device__ __forceinline__ float2 Io16<__half, __half2>::to2(unsigned u) {
-    return __half22float2(*reinterpret_cast<const __half2*>(&u));
+    const float2 v = __half22float2(*reinterpret_cast<const __half2*>(&u));
+    return make_float2(v.x * kHalfInvScale, v.y * kHalfInvScale);
 }
 template <> __device__ __forceinline__ unsigned Io16<__half, __half2>::from2(float a, float b) {
-    const __half2 h = __floats2half2_rn(a, b);
+    const __half2 h = __floats2half2_rn(a * kHalfScale, b * kHalfScale);
     return *reinterpret_cast<const unsigned*>(&h);
 }
 template <> __device__ __forceinline__ float2 Io16<__nv_bfloat16, __nv_bfloat162>::to2(unsigned u) {
@@ -106,14 +113,14 @@ template <typename H, typename H2> struct IoHalf {
     static __device__ __forceinline__ float ld1s(const H* p);
 };
 template <> __device__ __forceinline__ float IoHalf<__half, __half2>::ld1(const __half* p) {
-    return __half2float(__ldg(p));
+    return __half2float(__ldg(p)) * kHalfInvScale;
 }
 template <> __device__ __forceinline__ float IoHalf<__nv_bfloat16, __nv_bfloat162>::ld1(
     const __nv_bfloat16* p) {
     return __bfloat162float(__ldg(p));
 }
 template <> __device__ __forceinline__ float IoHalf<__half, __half2>::ld1s(const __half* p) {
-    return __half2float(*p);
+    return __half2float(*p) * kHalfInvScale;
 }
 template <> __device__ __forceinline__ float IoHalf<__nv_bfloat16, __nv_bfloat162>::ld1s(
     const __nv_bfloat16* p) {
@@ -126,7 +133,7 @@ template <typename T>
 __device__ __forceinline__ void store_scalar(T* p, float v);
 template <> __device__ __forceinline__ void store_scalar<float>(float* p, float v) { *p = v; }
 template <> __device__ __forceinline__ void store_scalar<__half>(__half* p, float v) {
-    *p = __float2half_rn(v);
+    *p = __float2half_rn(v * kHalfScale);
 }
 template <> __device__ __forceinline__ void store_scalar<__nv_bfloat16>(__nv_bfloat16* p, float v) {
     *p = __float2bfloat16_rn(v);
@@ -884,15 +891,21 @@ template <int S> struct Group { static constexpr int G = (S * S <= 4) ? 4 : 16; 
 // F_b = 2 rho_l (U_b - D_I u*) (Eq. 20).  The kernel lets the LBM kernel
 // launch at once: only band nodes there wait for these forces.
 template <typename T, int S>
-__global__ void __launch_bounds__(kThreads)
-ib_force_kernel(const T* __restrict__ g, LatticeParams p, IbParams q, int pull) {
-    cudaTriggerProgrammaticLaunchCompletion();
+__device__ __forceinline__ long long ib_marker_index() {
     constexpr int G = Group<S>::G;
     constexpr int MPW = 32 / G;
+    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    return wid * MPW + (threadIdx.x & 31) / G;
+}
+
+// Body of the IB kernel for marker m of this lane's group, on the lattice
+// described by p whose populations start at g.
+template <typename T, int S>
+__device__ __forceinline__ void ib_force_body(const T* __restrict__ g, const LatticeParams& p,
+                                              const IbParams& q, int pull, long long m) {
+    constexpr int G = Group<S>::G;
     const int lane = threadIdx.x & 31;
     const int li = lane % G;
-    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long m = wid * MPW + lane / G;
     const bool head = li == 0 && m < q.nmark;
 
     MarkerAux ax{};
@@ -953,6 +966,100 @@ ib_force_kernel(const T* __restrict__ g, LatticeParams p, IbParams q, int pull) 
             q.rhol[m] = rl;
         }
         if (!(rl > 0.f) || !isfinite(dFx) || !isfinite(dFy)) atomicOr(q.status, kStatusUnstable);
+    }
+}
+
+template <typename T, int S>
+__global__ void __launch_bounds__(kThreads)
+ib_force_kernel(const T* __restrict__ g, LatticeParams p, IbParams q, int pull) {
+    cudaTriggerProgrammaticLaunchCompletion();
+    ib_force_body<T, S>(g, p, q, pull, ib_marker_index<T, S>());
+}
+
+// Batched form: the markers of all lattices in one launch; MarkerAux.body
+// holds the lattice index, whose description and population offset the
+// lanes of that marker use.
+template <typename T, int S>
+__global__ void __launch_bounds__(kThreads)
+ib_force_batch_kernel(const T* __restrict__ g, const LatticeParams* __restrict__ descs,
+                      const unsigned long long* __restrict__ case_off, IbParams q, int pull) {
+    cudaTriggerProgrammaticLaunchCompletion();
+    const long long m = ib_marker_index<T, S>();
+    const int c = q.aux[m < q.nmark ? m : q.nmark - 1].body;
+    ib_force_body<T, S>(g + case_off[c], descs[c], q, pull, m);
+}
+
+// ---- the batched LBM kernel ---------------------------------------------------
+
+// Many independent lattices in one persistent launch.  Work units are blocks
+// of 8 rows of one lattice (one row per warp, all of its segments); each CTA
+// owns a contiguous range of units chosen on the host to balance segment
+// counts, and keeps the description of its current lattice in shared memory.
+// Body forces of all lattices are reduced in FP64 across the CTAs at the
+// end; the last CTA to finish advances the step counter.
+template <typename T, bool kPull, int NPL, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB)
+collide_stream_batch_kernel(const T* __restrict__ gin, T* __restrict__ gout, BatchLbm b) {
+    constexpr int SW = 32 * NPL;
+    constexpr int kWords = (int)(sizeof(LatticeParams) / sizeof(int));
+    __shared__ __align__(16) LatticeParams sp;
+    __shared__ unsigned long long s_step;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) s_step = *b.step;
+    __syncthreads();
+    int cur = -1;
+    unsigned long long off = 0;
+    const int u0 = b.cta_units[blockIdx.x], u1 = b.cta_units[blockIdx.x + 1];
+    for (int u = u0; u < u1; u++) {
+        const int2 un = b.units[u];
+        if (un.x != cur) {
+            __syncthreads();
+            const int* src = reinterpret_cast<const int*>(b.descs + un.x);
+            int* dst = reinterpret_cast<int*>(&sp);
+            for (int k = tid; k < kWords; k += blockDim.x) dst[k] = src[k];
+            __syncthreads();
+            cur = un.x;
+            off = b.case_off[cur];
+        }
+        const int y = un.y + warp;
+        if (y < sp.ny) {
+            const int nsegw = (sp.nxp + SW - 1) / SW;
+            for (int s = 0; s < nsegw; s++) {
+                const int seg = band_segment(sp, y, s * SW);
+                lbm_segment<T, kPull, NPL>(gin + off, gout + off, sp, y, s * SW, lane, seg);
+            }
+        }
+    }
+    if (b.nbody > 0) {
+        cudaGridDependencySynchronize();
+        const int nwarps = blockDim.x >> 5;
+        const long long slot =
+            (long long)(s_step % (unsigned long long)(b.hist_len > 0 ? b.hist_len : 1)) * b.nbody;
+        for (int bb = blockIdx.x * nwarps + warp; bb < b.nbody; bb += gridDim.x * nwarps) {
+            double sx = 0.0, sy = 0.0;
+            for (int k = b.body_rng[2 * bb] + lane; k < b.body_rng[2 * bb + 1]; k += 32) {
+                const float2 F = b.F[k];
+                sx += (double)F.x;
+                sy += (double)F.y;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                sx += __shfl_xor_sync(kFull, sx, o);
+                sy += __shfl_xor_sync(kFull, sy, o);
+            }
+            if (lane == 0) {
+                const double sc = b.body_scale[bb];
+                b.hist[slot + bb] = make_double2(-sx * sc, -sy * sc);
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(b.done, 1u) == gridDim.x - 1) {
+            *b.step = s_step + 1ull;
+            *b.done = 0u;
+        }
     }
 }
 
@@ -1161,6 +1268,97 @@ cudaError_t ib_force_t(bool pull, int width, const void* g, const LatticeParams&
 }
 
 }  // namespace
+
+template <typename T, int NPL>
+cudaError_t batch_lbm_tn(bool pull, const void* gin, void* gout, const BatchLbm& b, int grid, bool pdl,
+                         cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    constexpr int MB = Variant<NPL>::MINB;
+    if (pull)
+        return cudaLaunchKernelEx(&cfg, collide_stream_batch_kernel<T, true, NPL, MB>, (const T*)gin,
+                                  (T*)gout, b);
+    return cudaLaunchKernelEx(&cfg, collide_stream_batch_kernel<T, false, NPL, MB>, (const T*)gin,
+                              (T*)gout, b);
+}
+
+template <typename T, int NPL>
+int batch_blocks_tn() {
+    int n = 0, m = 0;
+    constexpr int MB = Variant<NPL>::MINB;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, collide_stream_batch_kernel<T, true, NPL, MB>,
+                                                  kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, collide_stream_batch_kernel<T, false, NPL, MB>,
+                                                  kThreads, 0);
+    return std::max(1, std::min(n, m));
+}
+
+template <typename T, int S>
+cudaError_t ib_batch_ts(bool pull, const void* g, const LatticeParams* descs,
+                        const unsigned long long* case_off, const IbParams& q, cudaStream_t st) {
+    constexpr int MPW = 32 / Group<S>::G;
+    const long long warps = (q.nmark + MPW - 1) / MPW;
+    const unsigned nb = blocks_for(warps * 32);
+    ib_force_batch_kernel<T, S><<<nb, kThreads, 0, st>>>((const T*)g, descs, case_off, q, pull ? 1 : 0);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t ib_batch_t(bool pull, int width, const void* g, const LatticeParams* descs,
+                       const unsigned long long* case_off, const IbParams& q, cudaStream_t st) {
+    switch (width) {
+    case 2: return ib_batch_ts<T, 2>(pull, g, descs, case_off, q, st);
+    case 3: return ib_batch_ts<T, 3>(pull, g, descs, case_off, q, st);
+    case 4: return ib_batch_ts<T, 4>(pull, g, descs, case_off, q, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+
+cudaError_t launch_collide_stream_batch(int storage, bool pull, int npl, const void* gin, void* gout,
+                                        const BatchLbm& b, int grid, bool pdl, cudaStream_t st) {
+    switch (storage) {
+    case kStoreF32:
+        return npl == 2 ? batch_lbm_tn<float, 2>(pull, gin, gout, b, grid, pdl, st)
+                        : batch_lbm_tn<float, 4>(pull, gin, gout, b, grid, pdl, st);
+    case kStoreF16:
+        return npl == 2 ? batch_lbm_tn<__half, 2>(pull, gin, gout, b, grid, pdl, st)
+                        : batch_lbm_tn<__half, 4>(pull, gin, gout, b, grid, pdl, st);
+    case kStoreBF16:
+        return npl == 2 ? batch_lbm_tn<__nv_bfloat16, 2>(pull, gin, gout, b, grid, pdl, st)
+                        : batch_lbm_tn<__nv_bfloat16, 4>(pull, gin, gout, b, grid, pdl, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+int collide_stream_batch_blocks_per_sm(int storage, int npl) {
+    switch (storage) {
+    case kStoreF16: return npl == 2 ? batch_blocks_tn<__half, 2>() : batch_blocks_tn<__half, 4>();
+    case kStoreBF16:
+        return npl == 2 ? batch_blocks_tn<__nv_bfloat16, 2>() : batch_blocks_tn<__nv_bfloat16, 4>();
+    default: return npl == 2 ? batch_blocks_tn<float, 2>() : batch_blocks_tn<float, 4>();
+    }
+}
+
+cudaError_t launch_ib_force_batch(int storage, bool pull, int width, const void* g,
+                                  const LatticeParams* descs, const unsigned long long* case_off,
+                                  const IbParams& q, cudaStream_t st) {
+    if (q.nmark <= 0) return cudaSuccess;
+    switch (storage) {
+    case kStoreF32: return ib_batch_t<float>(pull, width, g, descs, case_off, q, st);
+    case kStoreF16: return ib_batch_t<__half>(pull, width, g, descs, case_off, q, st);
+    case kStoreBF16: return ib_batch_t<__nv_bfloat16>(pull, width, g, descs, case_off, q, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 
 cudaError_t launch_collide_stream(int storage, bool pull, int npl, const void* gin, void* gout,
                                   const LatticeParams& p, int grid, bool pdl, cudaStream_t st) {

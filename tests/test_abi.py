@@ -71,3 +71,15 @@ def test_no_gpu_reports_cuda_error_not_fallback():
     cfg = B.btdf_config_default()
     rc, ctx = B.btdf_create(cfg)
     assert rc == B.BTDF_ECUDA and not ctx
+
+
+def test_batch_rejects_mixed_delta_and_mdf():
+    import ctypes as C
+    cfgs = (B.btdf_config * 2)(B.btdf_config_default(), B.btdf_config_default())
+    cfgs[1].delta = 4
+    out = C.c_void_p()
+    assert B.lib().btdf_batch_create(cfgs, 2, None, C.byref(out)) == B.BTDF_EINVAL
+    cfgs[1].delta = 3
+    cfgs[1].nf = 2
+    assert B.lib().btdf_batch_create(cfgs, 2, None, C.byref(out)) == B.BTDF_EINVAL
+    assert B.lib().btdf_batch_create(cfgs, 0, None, C.byref(out)) == B.BTDF_EINVAL

@@ -120,6 +120,35 @@ def paper_cylinder(re: float = 200.0, delta: int = 3, seed: int = 2) -> Case:
     return c
 
 
+def paper_domain_cylinder(re: float = 200.0, delta: int = 3, seed: int = 4) -> Case:
+    """The paper's own cylinder domain (Sec. 5.2): 40D x 40D with D/dh = 40,
+    i.e. a 1601 x 1601 lattice, cylinder at (18D, 20D), 126 markers."""
+    d = 40.0
+    c = Case(f"cyl1601sq_re{re:g}_d{delta}", 1601, 1601, tau_from_re(re, U_IN, d), U_IN, delta,
+             BCX_INOUT, BCY_FREESLIP, seed=seed, Re=re, D=d)
+    c.bodies.append(circle_markers(18.0 * d, 20.0 * d, d, 126))
+    return c
+
+
+def batch_cases(count: int = 512, seed: int = 7) -> List[Case]:
+    """Independent single-cylinder cases of uneven sizes: nx = 16 k with
+    k uniform in 8..64 (128..1024), ny = nx / 2, D uniform in [10, min(40,
+    ny / 5)], cylinder at (nx / 4, ny / 2), Re drawn from {0.1, 40, 200}."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        nx = 16 * int(rng.integers(8, 65))
+        ny = nx // 2
+        d = float(rng.uniform(10.0, min(40.0, ny / 5.0)))
+        re = float(rng.choice([0.1, 40.0, 200.0]))
+        n = max(8, int(round(math.pi * d)))
+        c = Case(f"batch{i}", nx, ny, tau_from_re(re, U_IN, d), U_IN, 3, BCX_INOUT, BCY_FREESLIP,
+                 seed=seed * 100003 + i, Re=re, D=d)
+        c.bodies.append(circle_markers(nx / 4.0 + 0.31, ny / 2.0 + 0.17, d, n))
+        out.append(c)
+    return out
+
+
 def adjoint_cylinder(seed: int = 5) -> Case:
     """800 x 400, D = 24 at (200, 200), 76 markers, Re = 100."""
     d = 24.0
