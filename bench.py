@@ -62,8 +62,12 @@ def measured_peaks():
 
 
 def kernel_source_hash():
-    p = os.path.join(ROOT, "paper_1806_09403_gb300", "csrc", "btdf_kernels.cu")
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+    """First 16 hex digits of the SHA-256 of the forward kernels' sources
+    (btdf_kernels.cu followed by btdf_device.cuh)."""
+    h = hashlib.sha256()
+    for f in ("btdf_kernels.cu", "btdf_device.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1806_09403_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def ncu_traffic(workload, storage):

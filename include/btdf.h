@@ -97,7 +97,8 @@ typedef enum {
 typedef struct {
     int32_t nx, ny;        /* lattice size, >= 4 each */
     double tau;            /* BGK relaxation time, > 0.5 (tau = 0.5 + 3 nu) */
-    double u_in;           /* inlet speed for BTDF_BCX_INOUT */
+    double u_in;           /* inlet speed for BTDF_BCX_INOUT; the value at creation is
+                              also the reference velocity of the stored deviations */
     int32_t delta;         /* btdf_delta */
     int32_t nf;            /* forcing passes per step, 1 = BTDF/DF, > 1 = MDF (Sec. 3.2) */
     int32_t storage;       /* btdf_storage */
@@ -138,6 +139,19 @@ int btdf_add_markers(btdf_ctx *ctx, int32_t n, const double *X, const double *Y,
 /* Replaces the prescribed marker velocities U_b of one body (host arrays of
  * that body's marker count).  Asynchronous on the context stream. */
 int btdf_set_marker_velocity(btdf_ctx *ctx, int32_t body, const double *Ubx, const double *Uby);
+
+/* Changes the inlet speed of BTDF_BCX_INOUT (the non-equilibrium
+ * extrapolation target, Sec. 5.2 inflow) without touching the stored state:
+ * the reference velocity of the stored deviations stays the creation-time
+ * u_in, so a checkpoint still loads as the same physical state.
+ * Synchronizes.  Errors: EINVAL (|u_in| >= 0.5 or not finite). */
+int btdf_set_inflow(btdf_ctx *ctx, double u_in);
+
+/* Moves the markers of one body to (X[l], Y[l]) (host arrays of the body's
+ * marker count) and re-evaluates its weights and the spreading table; ds,
+ * drs and the velocities are kept.  The force history restarts at the
+ * current step.  Synchronizes.  Errors: EINVAL (bad body, marker outside). */
+int btdf_move_markers(btdf_ctx *ctx, int32_t body, const double *X, const double *Y);
 
 /* Advances nsteps time steps (Algorithm 1), asynchronously on the context
  * stream.  Requires btdf_init_fields or btdf_load_state first (ESTATE). */
@@ -201,6 +215,40 @@ int btdf_tune(btdf_ctx *ctx, int32_t variant, int32_t grid_blocks);
 
 /* Bytes of device memory the context holds. */
 int btdf_device_bytes(const btdf_ctx *ctx, size_t *bytes);
+
+/* ---- discrete adjoint of a time window -----------------------------------
+ * Objective: the drag coefficient averaged over the next nsteps steps from the
+ * current state,
+ *   J = (1 / nsteps) sum_n Cd^n,   Cd^n = Fx^n / (u_in^2 dref / 2),
+ * with Fx^n the x force on the selected body (Eq. 27; body = -1: the sum over
+ * all bodies) in step n.  Gradients are taken with respect to the inlet speed
+ * u_in (entering the inlet extrapolation and the normalization; tau fixed)
+ * and every marker position (through the delta functions of Eq. 14 in both
+ * interpolation and spreading; ds and drs fixed).  The reverse sweep is the
+ * exact discrete adjoint of the FP32 step (collision with the Guo term, pull
+ * streaming with the wall, inlet and outlet rules, Eqs. 14, 15, 20).
+ *
+ * btdf_adjoint_forward runs the window from the current state on private
+ * buffers, keeping a checkpoint every `every` steps and the Lagrangian forces
+ * of every step, and returns J.  The context's own state, step counter and
+ * force history are not changed.  Requires nf = 1, FP32 storage, at least
+ * one body, dref > 0, u_in != 0, and, with an inlet, no marker support on
+ * columns 0 or nx-1.  Device memory: (ceil(nsteps/every) + every + 2) states
+ * of 36 * nxp * ny bytes plus 8 * nsteps * markers bytes, held until
+ * btdf_adjoint_release or btdf_destroy.
+ * Errors: EINVAL, ESTATE (no fields or no bodies), ENOMEM, EUNSTABLE.
+ *
+ * btdf_adjoint_backward reverses the last forward window: segments are
+ * recomputed from their checkpoints, then each step is reversed by three
+ * kernels (collision and boundary folds, marker forces and positions,
+ * interpolation at the band nodes).  Outputs (host, any may be NULL):
+ * dJdU = dJ/du_in, dJdX[l], dJdY[l] = dJ/dX_l, dJ/dY_l for every marker in the
+ * order the markers were added.  Setting the inflow, moving markers or
+ * changing marker velocities invalidates the window (ESTATE).  Synchronizes. */
+int btdf_adjoint_forward(btdf_ctx *ctx, int64_t nsteps, int32_t every, int32_t body, double dref,
+                         double *J);
+int btdf_adjoint_backward(btdf_ctx *ctx, double *dJdU, double *dJdX, double *dJdY);
+int btdf_adjoint_release(btdf_ctx *ctx);
 
 /* ---- batched form --------------------------------------------------------
  * Many independent lattices (each with its own size, relaxation time,

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libbtdf.so")
 SOURCES = ["btdf_kernels.cu", "btdf_api.cu", "btdf_static.cu", "btdf_tables.cu",
-           "btdf_batch.cu"]
+           "btdf_batch.cu", "btdf_adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

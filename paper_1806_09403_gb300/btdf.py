@@ -36,7 +36,8 @@ EXPORTS = [
     "btdf_batch_create", "btdf_batch_destroy", "btdf_batch_init_fields", "btdf_batch_add_markers",
     "btdf_batch_body_count", "btdf_batch_body_lattice", "btdf_batch_tune", "btdf_batch_step",
     "btdf_batch_sync", "btdf_batch_step_count", "btdf_batch_read_forces", "btdf_batch_read_field",
-    "btdf_batch_last_error",
+    "btdf_batch_last_error", "btdf_set_inflow", "btdf_move_markers", "btdf_adjoint_forward",
+    "btdf_adjoint_backward", "btdf_adjoint_release",
 ]
 STATIC_MAX_MARKERS = 2048
 STATE_HEADER_BYTES = 40
@@ -121,6 +122,12 @@ def lib() -> C.CDLL:
     L.btdf_batch_step_count.restype = C.c_int64
     L.btdf_batch_read_forces.argtypes = [vp, C.c_int32, C.c_int64, C.c_int64, vp, vp]
     L.btdf_batch_read_field.argtypes = [vp, C.c_int32, C.c_int32, vp, C.c_int32]
+    L.btdf_set_inflow.argtypes = [ctxp, C.c_double]
+    L.btdf_move_markers.argtypes = [ctxp, C.c_int32, _dp, _dp]
+    L.btdf_adjoint_forward.argtypes = [ctxp, C.c_int64, C.c_int32, C.c_int32, C.c_double,
+                                       C.POINTER(C.c_double)]
+    L.btdf_adjoint_backward.argtypes = [ctxp, C.POINTER(C.c_double), vp, vp]
+    L.btdf_adjoint_release.argtypes = [ctxp]
     L.btdf_batch_last_error.argtypes = [vp]
     L.btdf_batch_last_error.restype = C.c_char_p
     _lib = L
@@ -308,6 +315,40 @@ class Lattice:
         n = C.c_size_t()
         self._check(lib().btdf_device_bytes(self._ctx, C.byref(n)), "btdf_device_bytes")
         return n.value
+
+    def set_inflow(self, u_in):
+        self._check(lib().btdf_set_inflow(self._ctx, float(u_in)), "btdf_set_inflow")
+
+    def move_markers(self, body, X, Y):
+        self._check(lib().btdf_move_markers(self._ctx, int(body), _f64(X), _f64(Y)),
+                    "btdf_move_markers")
+
+    @property
+    def marker_count(self) -> int:
+        return int(sum(self.body_markers))
+
+    def body_first_marker(self, body) -> int:
+        return int(sum(self.body_markers[:body]))
+
+    def adjoint_forward(self, nsteps, every=50, body=-1, dref=1.0) -> float:
+        """Window-averaged drag coefficient over the next nsteps steps
+        (btdf_adjoint_forward); keeps the tape for adjoint_backward."""
+        J = C.c_double()
+        self._check(lib().btdf_adjoint_forward(self._ctx, int(nsteps), int(every), int(body),
+                                               float(dref), C.byref(J)), "btdf_adjoint_forward")
+        return J.value
+
+    def adjoint_backward(self):
+        """(dJ/du_in, dJ/dX[markers], dJ/dY[markers]) of the last forward window."""
+        n = self.marker_count
+        dX, dY = np.zeros(n), np.zeros(n)
+        dU = C.c_double()
+        self._check(lib().btdf_adjoint_backward(self._ctx, C.byref(dU), dX.ctypes.data,
+                                                dY.ctypes.data), "btdf_adjoint_backward")
+        return dU.value, dX, dY
+
+    def adjoint_release(self):
+        self._check(lib().btdf_adjoint_release(self._ctx), "btdf_adjoint_release")
 
 
 def _case_config(case, storage=BTDF_F32, history_len=4096, layout=None) -> btdf_config:

@@ -46,6 +46,35 @@ double paper_drs(int kind) { return kind == 2 ? 1.4 : kind == 3 ? 1.9 : 2.6; }
 
 size_t elem_bytes(int storage) { return storage == kStoreF32 ? 4 : 2; }
 
+// Device buffers and bookkeeping of one adjoint window (btdf_adjoint_*).
+struct AdjointTape {
+    bool pending = false;        // a forward window whose checkpoints are valid
+    bool post0 = false;          // the window starts from post-streaming populations
+    int64_t nsteps = 0;
+    int every = 0, nck = 0;      // checkpoint spacing and count
+    int body = -1;
+    double dref = 0.0, J = 0.0;
+    size_t state_elems = 0;      // floats per state
+    float* ck = nullptr;         // [nck] states g^{j every}
+    float* seg = nullptr;        // [every] states of the segment being reversed
+    float* lam[2] = {nullptr, nullptr};
+    float2* Fall = nullptr;      // [nsteps * nmark] Lagrangian forces of every step
+    float2* Us = nullptr;        // IB diagnostics of the recomputed steps (unused)
+    float* rhol = nullptr;
+    AdjMarker* am = nullptr;
+    float* cscale = nullptr;
+    float2* objw = nullptr;
+    int* band_keys = nullptr;
+    float* fbar_band = nullptr;
+    float2* Fbar_band = nullptr;
+    float4* mbar = nullptr;
+    double* acc = nullptr;       // [2 nmark + 1]: dJ/dX, dJ/dY, inlet part of dJ/dU
+    size_t bytes = 0;
+    int cap_ck = 0, cap_every = 0;
+    int64_t cap_F = 0;
+    int cap_mark = 0, cap_band = 0;
+};
+
 }  // namespace
 
 struct btdf_ctx {
@@ -95,6 +124,12 @@ struct btdf_ctx {
     size_t dev_bytes = 0;
     size_t marker_bytes = 0;           // part of dev_bytes held by marker data
     std::string err;
+
+    // Reference velocity U_r = (u_ref, 0) of the stored deviations: the
+    // creation-time inflow speed; btdf_set_inflow changes only cfg.u_in.
+    double u_ref = 0.0;
+    std::vector<int> band_keys;        // y * nseg + segment of each band segment
+    AdjointTape tape;
 };
 
 namespace {
@@ -156,6 +191,27 @@ void free_markers(btdf_ctx* ctx) {
     dfree(ctx, ctx->d_hist);
 }
 
+void free_tape(btdf_ctx* ctx) {
+    AdjointTape& T = ctx->tape;
+    dfree(ctx, T.ck);
+    dfree(ctx, T.seg);
+    dfree(ctx, T.lam[0]);
+    dfree(ctx, T.lam[1]);
+    dfree(ctx, T.Fall);
+    dfree(ctx, T.Us);
+    dfree(ctx, T.rhol);
+    dfree(ctx, T.am);
+    dfree(ctx, T.cscale);
+    dfree(ctx, T.objw);
+    dfree(ctx, T.band_keys);
+    dfree(ctx, T.fbar_band);
+    dfree(ctx, T.Fbar_band);
+    dfree(ctx, T.mbar);
+    dfree(ctx, T.acc);
+    ctx->dev_bytes -= T.bytes;
+    T = AdjointTape{};
+}
+
 bool is_tma(int v) { return v == kVarTma8x2 || v == kVarTma8x3 || v == kVarTma16x2; }
 
 LatticeParams lattice_params(const btdf_ctx* ctx) {
@@ -170,10 +226,10 @@ LatticeParams lattice_params(const btdf_ctx* ctx) {
     p.omega = (float)(1.0 / ctx->cfg.tau);
     p.guo = (float)(1.0 - 0.5 / ctx->cfg.tau);
     p.u_in = (float)ctx->cfg.u_in;
-    p.urx = (float)ctx->cfg.u_in;   // reference velocity of the stored deviations
+    p.urx = (float)ctx->u_ref;   // reference velocity of the stored deviations
     p.ury = 0.0f;
     {
-        const double tau = ctx->cfg.tau, Ux = ctx->cfg.u_in, Uy = 0.0;
+        const double tau = ctx->cfg.tau, Ux = ctx->u_ref, Uy = 0.0;
         p.one_m_omega = (float)(1.0 - 1.0 / tau);
         for (int a = 0; a < 9; a++) {
             const double w = a == 0 ? 4.0 / 9.0 : (a < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
@@ -337,6 +393,8 @@ int read_status(btdf_ctx* ctx) {
 // Static marker data and the node-centric spreading table (Eqs. 14, 15).
 int rebuild_markers(btdf_ctx* ctx) {
     drop_graphs(ctx);
+    ctx->tape.pending = false;
+    ctx->band_keys.clear();
     free_markers(ctx);
     const int nx = ctx->cfg.nx, ny = ctx->cfg.ny;
     const bool px = ctx->cfg.bc_x == kBcxPeriodic, py = ctx->cfg.bc_y == kBcyPeriodic;
@@ -356,7 +414,8 @@ int rebuild_markers(btdf_ctx* ctx) {
     }
     HostTables t;
     build_marker_tables(ctx->cfg.nx, ctx->cfg.ny, ctx->nseg, ctx->cfg.delta, ctx->width, px, py,
-                        ctx->cfg.u_in, descs, 0, t);
+                        ctx->u_ref, descs, 0, t);
+    ctx->band_keys.assign(t.seg_keys.begin(), t.seg_keys.end());
     for (int b = 0; b < nb; b++) {
         Body& B = ctx->bodies[b];
         B.wsum.assign(t.wsum.begin() + B.first, t.wsum.begin() + B.first + B.n);
@@ -406,6 +465,122 @@ int rebuild_markers(btdf_ctx* ctx) {
     CK(cudaStreamSynchronize(st));
     ctx->marker_bytes = ctx->dev_bytes - bytes_before;
     ctx->hist_from = ctx->steps;
+    return BTDF_OK;
+}
+
+// Marker positions must be finite and their support must touch the lattice.
+int check_positions(btdf_ctx* ctx, int n, const double* X, const double* Y) {
+    const int nx = ctx->cfg.nx, ny = ctx->cfg.ny;
+    const double half = 0.5 * ctx->width;
+    for (int l = 0; l < n; l++) {
+        if (!std::isfinite(X[l]) || !std::isfinite(Y[l]))
+            return fail(ctx, BTDF_EINVAL, "marker position not finite");
+        const bool inx = ctx->cfg.bc_x == kBcxPeriodic || (X[l] > -half && X[l] < nx - 1 + half);
+        const bool iny = ctx->cfg.bc_y == kBcyPeriodic || (Y[l] > -half && Y[l] < ny - 1 + half);
+        if (!inx || !iny) return fail(ctx, BTDF_EINVAL, "marker support lies outside the lattice");
+        if ((ctx->cfg.bc_x == kBcxPeriodic && std::fabs(X[l]) > 1e9) ||
+            (ctx->cfg.bc_y == kBcyPeriodic && std::fabs(Y[l]) > 1e9))
+            return fail(ctx, BTDF_EINVAL, "marker position out of range");
+    }
+    return BTDF_OK;
+}
+
+// ---- adjoint window ----
+
+// State n of the window as held by the tape while segment j is processed:
+// the checkpoint at the segment's start, the next checkpoint at its end,
+// the segment buffer in between.
+float* tape_state(const AdjointTape& T, int j, int64_t n) {
+    const int64_t s = (int64_t)j * T.every;
+    if (n == s) return T.ck + (size_t)j * T.state_elems;
+    if (j + 1 < T.nck && n == s + T.every) return T.ck + (size_t)(j + 1) * T.state_elems;
+    return T.seg + (size_t)(n - s - 1) * T.state_elems;
+}
+
+bool tape_pull(const AdjointTape& T, int64_t n) { return !(n == 0 && T.post0); }
+
+// One forward step of the window: the IB kernel writes F^n into the tape,
+// the LBM kernel spreads it and advances gin -> gout.  No body-force history
+// and no step counter: the context's own state is not touched.
+int tape_step(btdf_ctx* ctx, int64_t n, const float* gin, float* gout) {
+    AdjointTape& T = ctx->tape;
+    const bool pull = tape_pull(T, n);
+    float2* F = T.Fall + (size_t)n * ctx->nmark;
+    LatticeParams p = lattice_params(ctx);
+    p.F = F;
+    p.nbody = 0;
+    p.step = nullptr;
+    p.hist = nullptr;
+    IbParams q{};
+    q.nmark = ctx->nmark;
+    q.mk = ctx->d_mk;
+    q.aux = ctx->d_aux;
+    q.F_prev = nullptr;
+    q.F_out = F;
+    q.Us = T.Us;
+    q.rhol = T.rhol;
+    q.first_pass = 1;
+    q.status = ctx->d_status;
+    CK(launch_ib_force(kStoreF32, pull, ctx->width, gin, p, q, ctx->stream));
+    CK(launch_collide_stream(kStoreF32, pull, 4, gin, gout, p, (int)ctx->lbm_grid[0][pull ? 1 : 0], true,
+                             ctx->stream));
+    return BTDF_OK;
+}
+
+// Steps first .. last-1 of segment j.
+int tape_run(btdf_ctx* ctx, int j, int64_t first, int64_t last) {
+    const AdjointTape& T = ctx->tape;
+    for (int64_t n = first; n < last; n++) {
+        const int rc = tape_step(ctx, n, tape_state(T, j, n), tape_state(T, j, n + 1));
+        if (rc != BTDF_OK) return rc;
+    }
+    return BTDF_OK;
+}
+
+int tape_alloc(btdf_ctx* ctx, int nck, int every, int64_t nsteps) {
+    AdjointTape& T = ctx->tape;
+    const int nm = ctx->nmark, nb = (int)ctx->band_keys.size();
+    const size_t E = (size_t)9 * ctx->plane;
+    if (T.ck && T.state_elems == E && T.cap_ck >= nck && T.cap_every >= every && T.cap_F >= nsteps &&
+        T.cap_mark == nm && T.cap_band == nb)
+        return BTDF_OK;
+    free_tape(ctx);
+    T.state_elems = E;
+    const size_t before = ctx->dev_bytes;
+    auto bail = [&](cudaError_t e) {
+        const size_t got = ctx->dev_bytes - before;
+        T.bytes = got;
+        free_tape(ctx);
+        return e == cudaErrorMemoryAllocation ? fail(ctx, BTDF_ENOMEM, "adjoint tape does not fit")
+                                              : cuda_fail(ctx, e, "cudaMalloc");
+    };
+#define TA(ptr, count)                                                  \
+    do {                                                                \
+        cudaError_t e_ = dalloc(ctx, &(ptr), sizeof(*(ptr)) * (count)); \
+        if (e_ != cudaSuccess) return bail(e_);                         \
+    } while (0)
+    TA(T.ck, E * nck);
+    TA(T.seg, E * every);
+    TA(T.lam[0], E);
+    TA(T.lam[1], E);
+    TA(T.Fall, (size_t)nsteps * nm);
+    TA(T.Us, (size_t)nm);
+    TA(T.rhol, (size_t)nm);
+    TA(T.am, (size_t)nm);
+    TA(T.cscale, (size_t)nm);
+    TA(T.objw, (size_t)nm);
+    TA(T.band_keys, (size_t)std::max(nb, 1));
+    TA(T.fbar_band, (size_t)std::max(nb, 1) * kSeg * 9);
+    TA(T.Fbar_band, (size_t)std::max(nb, 1) * kSeg);
+    TA(T.mbar, (size_t)nm);
+    TA(T.acc, (size_t)2 * nm + 1);
+#undef TA
+    T.bytes = ctx->dev_bytes - before;
+    T.cap_ck = nck;
+    T.cap_every = every;
+    T.cap_F = nsteps;
+    T.cap_mark = nm;
+    T.cap_band = nb;
     return BTDF_OK;
 }
 
@@ -467,6 +642,7 @@ int btdf_create(const btdf_config* cfg, void* stream, btdf_ctx** out) {
     btdf_ctx* ctx = new (std::nothrow) btdf_ctx();
     if (!ctx) return BTDF_ENOMEM;
     ctx->cfg = c;
+    ctx->u_ref = c.u_in;
     ctx->stream = (cudaStream_t)stream;
     ctx->width = support_width(c.delta);
     ctx->nxp = (c.nx + 31) / 32 * 32;
@@ -519,6 +695,7 @@ int btdf_destroy(btdf_ctx* ctx) {
     if (ctx->stream || ctx->g[0]) cudaStreamSynchronize(ctx->stream);
     drop_graphs(ctx);
     free_markers(ctx);
+    free_tape(ctx);
     dfree(ctx, ctx->g[0]);
     dfree(ctx, ctx->g[1]);
     dfree(ctx, ctx->d_step);
@@ -570,20 +747,11 @@ int btdf_add_markers(btdf_ctx* ctx, int32_t n, const double* X, const double* Y,
     if (n < 1 || !X || !Y || !(ds > 0.0) || !std::isfinite(ds) || !std::isfinite(drs))
         return fail(ctx, BTDF_EINVAL, "need n >= 1 markers, positions and ds > 0");
     if ((long long)ctx->nmark + n > (1ll << 30)) return fail(ctx, BTDF_EINVAL, "too many markers");
-    const int nx = ctx->cfg.nx, ny = ctx->cfg.ny;
-    const double half = 0.5 * ctx->width;
-    for (int l = 0; l < n; l++) {
-        if (!std::isfinite(X[l]) || !std::isfinite(Y[l]))
-            return fail(ctx, BTDF_EINVAL, "marker position not finite");
+    for (int l = 0; l < n; l++)
         if ((Ubx && !std::isfinite(Ubx[l])) || (Uby && !std::isfinite(Uby[l])))
             return fail(ctx, BTDF_EINVAL, "marker velocity not finite");
-        const bool inx = ctx->cfg.bc_x == kBcxPeriodic || (X[l] > -half && X[l] < nx - 1 + half);
-        const bool iny = ctx->cfg.bc_y == kBcyPeriodic || (Y[l] > -half && Y[l] < ny - 1 + half);
-        if (!inx || !iny) return fail(ctx, BTDF_EINVAL, "marker support lies outside the lattice");
-        if ((ctx->cfg.bc_x == kBcxPeriodic && std::fabs(X[l]) > 1e9) ||
-            (ctx->cfg.bc_y == kBcyPeriodic && std::fabs(Y[l]) > 1e9))
-            return fail(ctx, BTDF_EINVAL, "marker position out of range");
-    }
+    const int rcp = check_positions(ctx, n, X, Y);
+    if (rcp != BTDF_OK) return rcp;
     Body B;
     B.first = ctx->nmark;
     B.n = n;
@@ -616,9 +784,10 @@ int btdf_set_marker_velocity(btdf_ctx* ctx, int32_t body, const double* Ubx, con
         B.Ubx[l] = Ubx[l];
         B.Uby[l] = Uby[l];
         MarkerAux& A = ctx->aux_host[B.first + l];
-        A.ubx_rel = (float)(Ubx[l] - ctx->cfg.u_in * B.wsum[l]);
+        A.ubx_rel = (float)(Ubx[l] - ctx->u_ref * B.wsum[l]);
         A.uby_rel = (float)Uby[l];
     }
+    ctx->tape.pending = false;
     CK(cudaMemcpyAsync(ctx->d_aux + B.first, ctx->aux_host.data() + B.first, sizeof(MarkerAux) * B.n,
                        cudaMemcpyHostToDevice, ctx->stream));
     // the host copy may change again before the copy runs: make it complete
@@ -814,6 +983,173 @@ int btdf_tune(btdf_ctx* ctx, int32_t variant, int32_t grid_blocks) {
     drop_graphs(ctx);
     ctx->variant = variant;
     ctx->grid_override = grid_blocks;
+    return BTDF_OK;
+}
+
+int btdf_set_inflow(btdf_ctx* ctx, double u_in) {
+    if (!ctx) return BTDF_EINVAL;
+    if (!std::isfinite(u_in) || std::fabs(u_in) >= 0.5) return fail(ctx, BTDF_EINVAL, "need |u_in| < 0.5");
+    CK(cudaStreamSynchronize(ctx->stream));
+    drop_graphs(ctx);   // the graphs hold the old value in their kernel arguments
+    ctx->cfg.u_in = u_in;
+    ctx->tape.pending = false;
+    return BTDF_OK;
+}
+
+int btdf_move_markers(btdf_ctx* ctx, int32_t body, const double* X, const double* Y) {
+    if (!ctx) return BTDF_EINVAL;
+    if (body < 0 || body >= (int)ctx->bodies.size() || !X || !Y)
+        return fail(ctx, BTDF_EINVAL, "bad body index or null positions");
+    Body& B = ctx->bodies[body];
+    const int rc = check_positions(ctx, B.n, X, Y);
+    if (rc != BTDF_OK) return rc;
+    CK(cudaStreamSynchronize(ctx->stream));
+    B.X.assign(X, X + B.n);
+    B.Y.assign(Y, Y + B.n);
+    return rebuild_markers(ctx);
+}
+
+int btdf_adjoint_forward(btdf_ctx* ctx, int64_t nsteps, int32_t every, int32_t body, double dref,
+                         double* J) {
+    if (!ctx) return BTDF_EINVAL;
+    if (!ctx->has_fields) return fail(ctx, BTDF_ESTATE, "call btdf_init_fields or btdf_load_state first");
+    if (ctx->nmark == 0) return fail(ctx, BTDF_ESTATE, "the objective needs at least one body");
+    if (ctx->cfg.nf != 1 || ctx->cfg.storage != BTDF_F32)
+        return fail(ctx, BTDF_EINVAL, "the adjoint supports nf = 1 with FP32 storage");
+    if (nsteps < 1 || every < 1 || nsteps > (1ll << 30))
+        return fail(ctx, BTDF_EINVAL, "need nsteps >= 1 and every >= 1");
+    if (!(dref > 0.0) || !std::isfinite(dref)) return fail(ctx, BTDF_EINVAL, "need dref > 0");
+    if (!(std::fabs(ctx->cfg.u_in) > 0.0)) return fail(ctx, BTDF_EINVAL, "Cd needs u_in != 0");
+    if (body < -1 || body >= (int)ctx->bodies.size()) return fail(ctx, BTDF_EINVAL, "bad body index");
+    if (ctx->cfg.bc_x == kBcxInout) {
+        const int S = ctx->width;
+        for (const Body& B : ctx->bodies)
+            for (int l = 0; l < B.n; l++) {
+                const int i0 = (int)std::floor(B.X[l] - 0.5 * S) + 1;
+                if (i0 < 1 || i0 + S - 1 > ctx->cfg.nx - 2)
+                    return fail(ctx, BTDF_EINVAL, "a marker support reaches the inlet or outlet column");
+            }
+    }
+    if (every > nsteps) every = (int32_t)nsteps;
+    const int nck = (int)((nsteps + every - 1) / every);
+    int rc = tape_alloc(ctx, nck, every, nsteps);
+    if (rc != BTDF_OK) return rc;
+    AdjointTape& T = ctx->tape;
+    T.pending = false;
+    T.nsteps = nsteps;
+    T.every = every;
+    T.nck = nck;
+    T.body = body;
+    T.dref = dref;
+    T.post0 = ctx->poststream;
+
+    // per-marker tables of the objective and of the position derivatives
+    const int nm = ctx->nmark;
+    std::vector<BodyDesc> descs;
+    std::vector<float> cscale(nm);
+    std::vector<float2> objw(nm, make_float2(0.f, 0.f));
+    const double q = 0.5 * ctx->cfg.u_in * ctx->cfg.u_in * dref;
+    for (int b = 0; b < (int)ctx->bodies.size(); b++) {
+        const Body& B = ctx->bodies[b];
+        descs.push_back(BodyDesc{B.n, B.ds, B.drs, B.X.data(), B.Y.data(), B.Ubx.data(), B.Uby.data(), b});
+        for (int l = 0; l < B.n; l++) {
+            cscale[B.first + l] = (float)(B.ds * B.drs);
+            if (body < 0 || body == b)   // Cd = -c sum F_x / (U^2 D / 2), averaged over the window
+                objw[B.first + l].x = (float)(-B.ds * B.drs / (q * (double)nsteps));
+        }
+    }
+    std::vector<AdjMarker> am;
+    build_adjoint_markers(ctx->cfg.nx, ctx->cfg.ny, ctx->cfg.delta, ctx->width,
+                          ctx->cfg.bc_x == kBcxPeriodic, ctx->cfg.bc_y == kBcyPeriodic, descs, am);
+    cudaStream_t st = ctx->stream;
+    CK(cudaMemcpyAsync(T.am, am.data(), sizeof(AdjMarker) * nm, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(T.cscale, cscale.data(), sizeof(float) * nm, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(T.objw, objw.data(), sizeof(float2) * nm, cudaMemcpyHostToDevice, st));
+    if (!ctx->band_keys.empty())
+        CK(cudaMemcpyAsync(T.band_keys, ctx->band_keys.data(), sizeof(int) * ctx->band_keys.size(),
+                           cudaMemcpyHostToDevice, st));
+
+    // forward window from the context's state, checkpoints every `every` steps
+    CK(cudaMemcpyAsync(T.ck, ctx->g[ctx->cur], sizeof(float) * T.state_elems, cudaMemcpyDeviceToDevice, st));
+    for (int j = 0; j < nck; j++) {
+        const int64_t s = (int64_t)j * every, e = std::min<int64_t>(s + every, nsteps);
+        rc = tape_run(ctx, j, s, e);
+        if (rc != BTDF_OK) return rc;
+    }
+    std::vector<float2> F((size_t)nsteps * nm);
+    CK(cudaMemcpyAsync(F.data(), T.Fall, sizeof(float2) * F.size(), cudaMemcpyDeviceToHost, st));
+    rc = read_status(ctx);
+    if (rc != BTDF_OK) return rc;
+    double acc = 0.0;
+    for (int64_t n = 0; n < nsteps; n++)
+        for (int b = 0; b < (int)ctx->bodies.size(); b++) {
+            if (body >= 0 && body != b) continue;
+            const Body& B = ctx->bodies[b];
+            double sx = 0.0;
+            for (int l = 0; l < B.n; l++) sx += (double)F[(size_t)n * nm + B.first + l].x;
+            acc += -sx * B.ds * B.drs;
+        }
+    T.J = acc / (q * (double)nsteps);
+    T.pending = true;
+    if (J) *J = T.J;
+    return BTDF_OK;
+}
+
+int btdf_adjoint_backward(btdf_ctx* ctx, double* dJdU, double* dJdX, double* dJdY) {
+    if (!ctx) return BTDF_EINVAL;
+    AdjointTape& T = ctx->tape;
+    if (!T.pending) return fail(ctx, BTDF_ESTATE, "no forward window to reverse");
+    cudaStream_t st = ctx->stream;
+    const int nm = ctx->nmark;
+    const size_t sb = sizeof(float) * T.state_elems;
+    CK(cudaMemsetAsync(T.acc, 0, sizeof(double) * (2 * (size_t)nm + 1), st));
+    CK(cudaMemsetAsync(T.lam[0], 0, sb, st));   // dJ/dg^N = 0
+    AdjParams q{};
+    q.nmark = nm;
+    q.nband = (int)ctx->band_keys.size();
+    q.mk = ctx->d_mk;
+    q.aux = ctx->d_aux;
+    q.am = T.am;
+    q.cscale = T.cscale;
+    q.band_keys = T.band_keys;
+    q.fbar_band = T.fbar_band;
+    q.Fbar_band = T.Fbar_band;
+    q.mbar = T.mbar;
+    q.objw = T.objw;
+    q.dJdX = T.acc;
+    q.dJdY = T.acc + nm;
+    q.dU = T.acc + 2 * nm;
+    int c = 0;
+    for (int j = T.nck - 1; j >= 0; j--) {
+        const int64_t s = (int64_t)j * T.every, e = std::min<int64_t>(s + T.every, T.nsteps);
+        // states g^{s+1} .. g^{e-1}; F^{e-1} is already on the tape
+        const int rc = tape_run(ctx, j, s, e - 1);
+        if (rc != BTDF_OK) return rc;
+        for (int64_t n = e - 1; n >= s; n--) {
+            LatticeParams p = lattice_params(ctx);
+            p.F = T.Fall + (size_t)n * nm;
+            CK(cudaMemsetAsync(T.lam[1 - c], 0, sb, st));
+            CK(launch_adjoint_step(tape_state(T, j, n), T.lam[c], T.lam[1 - c], p, q, ctx->width,
+                                   tape_pull(T, n), st));
+            c = 1 - c;
+        }
+    }
+    std::vector<double> acc(2 * (size_t)nm + 1);
+    CK(cudaMemcpyAsync(acc.data(), T.acc, sizeof(double) * acc.size(), cudaMemcpyDeviceToHost, st));
+    const int rc = read_status(ctx);
+    if (rc != BTDF_OK) return rc;
+    if (dJdU) *dJdU = acc[2 * (size_t)nm] - 2.0 * T.J / ctx->cfg.u_in;   // inlet + 1 / (U^2 D / 2)
+    for (int l = 0; l < nm; l++) {
+        if (dJdX) dJdX[l] = acc[l];
+        if (dJdY) dJdY[l] = acc[(size_t)nm + l];
+    }
+    return BTDF_OK;
+}
+
+int btdf_adjoint_release(btdf_ctx* ctx) {
+    if (!ctx) return BTDF_EINVAL;
+    CK(cudaStreamSynchronize(ctx->stream));
+    free_tape(ctx);
     return BTDF_OK;
 }
 

@@ -175,6 +175,36 @@ cudaError_t launch_init_equilibrium(int storage, void* g, const LatticeParams& p
 cudaError_t launch_read_field(int storage, bool pull, const void* g, const LatticeParams& p,
                               int kind, float* dst, cudaStream_t st);
 
+// ---- discrete adjoint ----
+
+// Per-marker 1-D weights and their derivatives with respect to the marker
+// position: W = wx[i] wy[j], dW/dX = dwx[i] wy[j], dW/dY = wx[i] dwy[j].
+struct AdjMarker {
+    float wx[4], wy[4], dwx[4], dwy[4];
+};
+
+struct AdjParams {
+    int nmark, nband;
+    const Marker* mk;
+    const MarkerAux* aux;
+    const AdjMarker* am;
+    const float* cscale;       // drs * ds of each marker's body
+    const int* band_keys;      // [nband] y * nseg + segment
+    float* fbar_band;          // [nband * kSeg * 9] dJ/df parked at band nodes
+    float2* Fbar_band;         // [nband * kSeg] dJ/dF (node force) at band nodes
+    float4* mbar;              // [nmark] (dJ/drho_l, dJ/dU*_l)
+    const float2* objw;        // [nmark] explicit dJ/dF_l of the objective
+    double* dJdX;              // [nmark] accumulated over the window
+    double* dJdY;
+    double* dU;                // inlet part of dJ/dU_in
+};
+
+// Launcher implemented in btdf_adjoint.cu: g = g^n (pull: post-collision,
+// else post-streaming), lam = dJ/dg^{n+1}, gbar = dJ/dg^n (zeroed by the
+// caller); p.F must hold the Lagrangian forces F^n of the step.
+cudaError_t launch_adjoint_step(const float* g, const float* lam, float* gbar, const LatticeParams& p,
+                                const AdjParams& q, int width, bool pull, cudaStream_t st);
+
 // ---- host-side static tables (btdf_tables.cu) ----
 
 // One rigid body as seen by the table builder; tag goes to MarkerAux.body.
@@ -196,6 +226,9 @@ struct HostTables {
 };
 
 double delta_fn(int kind, double r);
+double delta_deriv(int kind, double r);
+void build_adjoint_markers(int nx, int ny, int delta, int width, bool px, bool py,
+                           const std::vector<BodyDesc>& bodies, std::vector<AdjMarker>& out);
 void build_marker_tables(int nx, int ny, int nseg, int delta, int width, bool px, bool py,
                          double u_in, const std::vector<BodyDesc>& bodies, int marker_base,
                          HostTables& t);

@@ -30,6 +30,55 @@ double delta_fn(int kind, double r) {
     }
 }
 
+// d delta / dr of the same functions (Eqs. 37-39 differentiated; the 2-point
+// kernel takes the one-sided slope at its kinks).
+double delta_deriv(int kind, double r) {
+    const double a = std::fabs(r), sg = r < 0.0 ? -1.0 : 1.0;
+    switch (kind) {
+    case 2:
+        return a < 1.0 ? -sg : 0.0;
+    case 3:
+        if (a >= 1.5) return 0.0;
+        if (a > 0.5) return sg * (-0.5 - (1.0 - a) / (2.0 * std::sqrt(1.0 - 3.0 * (1.0 - a) * (1.0 - a))));
+        return sg * (-a / std::sqrt(1.0 - 3.0 * a * a));
+    case 4:
+        if (a >= 2.0) return 0.0;
+        if (a >= 1.0) return sg * (-2.0 - (6.0 - 4.0 * a) / std::sqrt(-7.0 + 12.0 * a - 4.0 * a * a)) / 8.0;
+        return sg * (-2.0 + (2.0 - 4.0 * a) / std::sqrt(1.0 + 4.0 * a - 4.0 * a * a)) / 8.0;
+    case 5:
+        return a < 2.0 ? -sg * (M_PI / 8.0) * std::sin(M_PI * a * 0.5) : 0.0;
+    default:
+        return 0.0;
+    }
+}
+
+void build_adjoint_markers(int nx, int ny, int delta, int width, bool px, bool py,
+                           const std::vector<BodyDesc>& bodies, std::vector<AdjMarker>& out) {
+    const int S = width;
+    out.clear();
+    for (const BodyDesc& B : bodies)
+        for (int l = 0; l < B.n; l++) {
+            const double X = B.X[l], Y = B.Y[l];
+            const int i0 = (int)std::floor(X - 0.5 * S) + 1;
+            const int j0 = (int)std::floor(Y - 0.5 * S) + 1;
+            AdjMarker A{};
+            for (int i = 0; i < S; i++) {
+                int x = i0 + i, y = j0 + i;
+                if (px) x = ((x % nx) + nx) % nx;
+                if (py) y = ((y % ny) + ny) % ny;
+                if (x >= 0 && x < nx) {
+                    A.wx[i] = (float)delta_fn(delta, (double)(i0 + i) - X);
+                    A.dwx[i] = (float)(-delta_deriv(delta, (double)(i0 + i) - X));   // d/dX
+                }
+                if (y >= 0 && y < ny) {
+                    A.wy[i] = (float)delta_fn(delta, (double)(j0 + i) - Y);
+                    A.dwy[i] = (float)(-delta_deriv(delta, (double)(j0 + i) - Y));
+                }
+            }
+            out.push_back(A);
+        }
+}
+
 void build_marker_tables(int nx, int ny, int nseg, int delta, int width, bool px, bool py,
                          double u_in, const std::vector<BodyDesc>& bodies, int marker_base,
                          HostTables& t) {

@@ -120,11 +120,13 @@ def paper_cylinder(re: float = 200.0, delta: int = 3, seed: int = 2) -> Case:
     return c
 
 
-def paper_domain_cylinder(re: float = 200.0, delta: int = 3, seed: int = 4) -> Case:
+def paper_domain_cylinder(re: float = 200.0, delta: int = 3, seed: int = 4,
+                          u: float = U_IN) -> Case:
     """The paper's own cylinder domain (Sec. 5.2): 40D x 40D with D/dh = 40,
-    i.e. a 1601 x 1601 lattice, cylinder at (18D, 20D), 126 markers."""
+    i.e. a 1601 x 1601 lattice, cylinder at (18D, 20D), 126 markers, inflow
+    speed u (the paper does not state it)."""
     d = 40.0
-    c = Case(f"cyl1601sq_re{re:g}_d{delta}", 1601, 1601, tau_from_re(re, U_IN, d), U_IN, delta,
+    c = Case(f"cyl1601sq_re{re:g}_d{delta}", 1601, 1601, tau_from_re(re, u, d), u, delta,
              BCX_INOUT, BCY_FREESLIP, seed=seed, Re=re, D=d)
     c.bodies.append(circle_markers(18.0 * d, 20.0 * d, d, 126))
     return c
