@@ -245,19 +245,8 @@ def batch_mode(args):
     bt = B.Batch.from_cases(cases, storage=storage, history_len=64, stream=stream.cuda_stream)
     bt.step(args.warmup)
     bt.sync()
-    # launch shape picked by timing each candidate on the batch itself
-    tune = {}
-    for v in (1, 2):
-        bt.tune(v)
-        bt.step(32)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        bt.step(64)
-        b.record(stream)
-        bt.sync()
-        tune[v] = a.elapsed_time(b) / 64
-    best = min(tune, key=tune.get)
-    bt.tune(best)
+    # launch shape picked by the library's autotuner on the batch itself
+    best, tune = bt.autotune(16, False)
     bt.step(32)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -306,6 +295,55 @@ def batch_mode(args):
     return 0
 
 
+def adjoint_mode(args):
+    """Adjoint window on the 800 x 400 cylinder (D = 24, 76 markers, Re = 100,
+    3-point delta): 500 steps after a 2000-step spin-up, a checkpoint every
+    50 steps.  Times the forward window (J) and the reverse sweep (dJ/dU and
+    dJ/dX, dJ/dY of every marker) through the C ABI."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import workloads as W
+    from paper_1806_09403_gb300 import btdf as B
+    case = W.adjoint_cylinder()
+    stream = torch.cuda.current_stream()
+    lat = B.Lattice.from_case(case, stream=stream.cuda_stream, history_len=1024)
+    lat.step(2000)
+    lat.sync()
+    nsteps, every = 500, 50
+    nodes = case.nx * case.ny
+    lat.adjoint_forward(nsteps, every, 0, case.D)   # warm-up (allocates the tape)
+    lat.adjoint_backward()
+    reps = max(1, min(args.steps, 20))
+    tf = tb = 0.0
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        J = lat.adjoint_forward(nsteps, every, 0, case.D)
+        t1 = time.perf_counter()
+        dU, dX, dY = lat.adjoint_backward()
+        t2 = time.perf_counter()
+        tf += t1 - t0
+        tb += t2 - t1
+    tf /= reps
+    tb /= reps
+    nm = len(case.bodies[0].X)
+    print(json.dumps({
+        "mode": "adjoint", "workload": "cylinder 800x400, D=24, 76 markers, Re=100 (tau=0.536), "
+                                      "3-point delta; window of 500 steps, checkpoint every 50",
+        "J": J, "dJdU": dU, "reps": reps,
+        "forward_ms": tf * 1e3, "backward_ms": tb * 1e3,
+        "forward_mlups": nodes * nsteps / tf / 1e6,
+        "backward_mlups": nodes * nsteps / tb / 1e6,
+        "backward_over_forward": tb / tf,
+        "gradient_entries": 1 + 2 * nm,
+        "central_fd_cost_over_adjoint": 2 * (1 + nm) * tf / (tf + tb),
+        "tape_device_mb": lat.device_bytes() / 1e6,
+    }))
+    return 0
+
+
 def our_arm(args):
     import torch
     world, rank, local = dist_setup(args)
@@ -343,27 +381,16 @@ def our_arm(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    # ---- kernel variant: each candidate timed like the timed region below ----
+    # ---- kernel variant: the library's autotuner times each candidate on
+    # this lattice (L2 evicted before every step, median of 32 steps) ----
     names = {1: "reg4", 2: "reg2", 3: "tma8x2", 4: "tma8x3", 5: "tma16x2", 6: "reg4pf", 7: "reg2pf"}
-    tune = {}
-    for v in (tuple(names) if args.variant == 0 else (args.variant,)):
-        try:
-            lat.tune(v, 0)
-        except B.BtdfError:
-            continue
-        lat.step(8)
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(64)]
-        for a, b in evs:
-            flush_l2()
-            a.record(stream)
-            lat.step(1)
-            b.record(stream)
-        lat.sync()
-        tune[names[v]] = sum(a.elapsed_time(b) for a, b in evs) / len(evs)
-    best_name = min(tune, key=tune.get)
-    best = {n: k for k, n in names.items()}[best_name]
-    lat.tune(best, 0)
+    if args.variant == 0:
+        best, tms = lat.autotune(32, True)
+        tune = {names[v]: t for v, t in tms.items()}
+    else:
+        best, tune = args.variant, {}
+        lat.tune(best, 0)
+    best_name = names[best]
 
     # ---- timed region: K steps, L2 flushed before each, per-step events ----
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -485,7 +512,9 @@ def our_arm(args):
                 "d2h_bytes_per_step": 16 if nb else 0,
                 "how": "per step: marker velocities H2D, one step, body force D2H, synchronous"},
         "gpu_launches": int(args.steps * (n_ib + n_lbm) // max(n_lbm, 1)),
-        "kernel_variant": {"chosen": best_name, "ms_per_step_flushed": tune},
+        "kernel_variant": {"chosen": best_name, "ms_per_step_flushed": tune,
+                           "tuner": "btdf_autotune: median of 32 steps per variant, L2 evicted "
+                                    "before each"},
         "clocks": clk.summary(),
         "graph_warm_mlups": warm,
         "cd_err_vs_fp64": cd_err,
@@ -505,7 +534,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-seconds", type=float, default=90.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="bench", choices=["bench", "kernel", "batch"])
+    ap.add_argument("--mode", default="bench", choices=["bench", "kernel", "batch", "adjoint"])
     ap.add_argument("--variant", type=int, default=0, choices=list(range(8)))
     ap.add_argument("--layout", default="rows", choices=["rows", "planes"])
     args = ap.parse_args()
@@ -517,6 +546,8 @@ def main():
         return kernel_mode(args)
     if args.mode == "batch":
         return batch_mode(args)
+    if args.mode == "adjoint":
+        return adjoint_mode(args)
     return our_arm(args)
 
 

@@ -216,6 +216,21 @@ int btdf_tune(btdf_ctx *ctx, int32_t variant, int32_t grid_blocks);
 /* Bytes of device memory the context holds. */
 int btdf_device_bytes(const btdf_ctx *ctx, size_t *bytes);
 
+/* Autotuner of the collide-stream launch: times every available variant of
+ * btdf_tune (1..7; the TMA variants only where tensor maps were encoded) on
+ * this context's own lattice, `steps` steps each after 3 untimed ones, every
+ * step (IB and LBM stage, overlapped as in btdf_step) between CUDA events on
+ * the context stream, with the L2 cache evicted before each step when
+ * flush_l2 != 0.  Keeps the variant with the lowest median step time.  The
+ * populations, the step counter, the force history and the last step's
+ * marker results are restored afterwards, so the simulation does not
+ * advance.  Outputs (may be NULL): *chosen, and ms[v] = median ms per step of
+ * variant v for v = 0..7 (-1 where not timed).  Needs temporary device memory
+ * for one copy of the populations and, with flush_l2, four times the L2 size.
+ * Synchronizes.  Errors: EINVAL (steps outside 1..100000), ESTATE (no fields),
+ * ENOMEM / ECUDA. */
+int btdf_autotune(btdf_ctx *ctx, int32_t steps, int32_t flush_l2, int32_t *chosen, float *ms);
+
 /* ---- discrete adjoint of a time window -----------------------------------
  * Objective: the drag coefficient averaged over the next nsteps steps from the
  * current state,
@@ -278,6 +293,8 @@ int btdf_batch_body_lattice(const btdf_batch *b, int32_t body, int32_t *lattice)
 /* Collide-stream launch shape: 1 = 4 nodes per lane, 2 = 2 nodes per lane,
  * 0 = default (1).  Results do not depend on it. */
 int btdf_batch_tune(btdf_batch *b, int32_t variant);
+/* As btdf_autotune, over the batch's launch shapes 1 and 2; ms[0..2]. */
+int btdf_batch_autotune(btdf_batch *b, int32_t steps, int32_t flush_l2, int32_t *chosen, float *ms);
 int btdf_batch_step(btdf_batch *b, int64_t nsteps);
 int btdf_batch_sync(btdf_batch *b);
 int64_t btdf_batch_step_count(const btdf_batch *b);

@@ -446,6 +446,28 @@ static void ib_stage(ora_sim *s)
 /* Source node of a pull along one axis; -1 when it lies off a bounded axis. */
 static int src_axis(int i, int n, int periodic) { return map_axis(i, n, periodic); }
 
+/* Inlet x = 0 by non-equilibrium extrapolation from column 1 of the
+ * post-streaming populations: f(0) = f_eq(rho_1, (u_in, 0)) + f(1) - f_eq(rho_1, u_1). */
+static void inlet_column(ora_sim *s)
+{
+    const int nx = s->nx, ny = s->ny;
+    double *fn = s->f;
+    for (int y = 0; y < ny; y++) {
+        double r1, u1x, u1y, e_in[9], e_1[9];
+        const double *f1 = &fn[((size_t)y * nx + 1) * 9];
+        double *f0 = &fn[((size_t)y * nx) * 9];
+        node_moments(f1, &r1, &u1x, &u1y);
+        oracle_feq(r1, s->u_in, 0.0, e_in);
+        oracle_feq(r1, u1x, u1y, e_1);
+        for (int a = 0; a < 9; a++) f0[a] = e_in[a] + f1[a] - e_1[a];
+    }
+}
+
+void oracle_apply_inlet(ora_sim *s)
+{
+    if (s->bcx == 1) inlet_column(s);
+}
+
 static void stream_and_bc(ora_sim *s)
 {
     const int nx = s->nx, ny = s->ny;
@@ -484,14 +506,7 @@ static void stream_and_bc(ora_sim *s)
         }
     }
     if (s->bcx == 1) {
-        for (int y = 0; y < ny; y++) {
-            /* inlet: non-equilibrium extrapolation from column 1 */
-            double r1, u1x, u1y, e_in[9], e_1[9];
-            node_moments(&FN(1, y, 0), &r1, &u1x, &u1y);
-            oracle_feq(r1, s->u_in, 0.0, e_in);
-            oracle_feq(r1, u1x, u1y, e_1);
-            for (int a = 0; a < 9; a++) FN(0, y, a) = e_in[a] + FN(1, y, a) - e_1[a];
-        }
+        inlet_column(s);
         for (int y = 0; y < ny; y++)          /* outlet: zero gradient */
             for (int a = 0; a < 9; a++) FN(nx - 1, y, a) = FN(nx - 2, y, a);
     }

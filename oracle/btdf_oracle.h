@@ -37,6 +37,12 @@ void oracle_init_fields(ora_sim *s, const double *rho, const double *ux, const d
 /* Raw population access, ny*nx*9 doubles, AoS. */
 void oracle_get_pops(const ora_sim *s, double *out);
 void oracle_set_pops(ora_sim *s, const double *in);
+/* Re-applies the inlet rule (non-equilibrium extrapolation from column 1,
+ * Sec. 5.2 inflow) to the current post-streaming populations with the
+ * simulation's own u_in; no effect without an inlet.  A state taken from a
+ * simulation with another inlet speed then continues as if that speed had
+ * been in force at the last streaming. */
+void oracle_apply_inlet(ora_sim *s);
 
 /* One body of n markers; drs <= 0 takes the paper's constant for the delta.
  * Returns the body index. */

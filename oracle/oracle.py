@@ -48,6 +48,7 @@ def lib() -> C.CDLL:
     L.oracle_init_fields.argtypes = [vp, _dp, _dp, _dp]
     L.oracle_get_pops.argtypes = [vp, _dp]
     L.oracle_set_pops.argtypes = [vp, _dp]
+    L.oracle_apply_inlet.argtypes = [vp]
     L.oracle_add_body.restype = C.c_int
     L.oracle_add_body.argtypes = [vp, C.c_int, _dp, _dp, _dp, _dp, C.c_double, C.c_double]
     L.oracle_set_marker_velocity.argtypes = [vp, C.c_int, _dp, _dp]
@@ -178,6 +179,9 @@ class Sim:
 
     def set_pops(self, f):
         lib().oracle_set_pops(self._p, _c(f).ravel())
+
+    def apply_inlet(self):
+        lib().oracle_apply_inlet(self._p)
 
     def force_field(self):
         sh = (self.ny, self.nx)

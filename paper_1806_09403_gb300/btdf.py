@@ -37,7 +37,7 @@ EXPORTS = [
     "btdf_batch_body_count", "btdf_batch_body_lattice", "btdf_batch_tune", "btdf_batch_step",
     "btdf_batch_sync", "btdf_batch_step_count", "btdf_batch_read_forces", "btdf_batch_read_field",
     "btdf_batch_last_error", "btdf_set_inflow", "btdf_move_markers", "btdf_adjoint_forward",
-    "btdf_adjoint_backward", "btdf_adjoint_release",
+    "btdf_adjoint_backward", "btdf_adjoint_release", "btdf_autotune", "btdf_batch_autotune",
 ]
 STATIC_MAX_MARKERS = 2048
 STATE_HEADER_BYTES = 40
@@ -128,6 +128,8 @@ def lib() -> C.CDLL:
                                        C.POINTER(C.c_double)]
     L.btdf_adjoint_backward.argtypes = [ctxp, C.POINTER(C.c_double), vp, vp]
     L.btdf_adjoint_release.argtypes = [ctxp]
+    L.btdf_autotune.argtypes = [ctxp, C.c_int32, C.c_int32, C.POINTER(C.c_int32), vp]
+    L.btdf_batch_autotune.argtypes = [vp, C.c_int32, C.c_int32, C.POINTER(C.c_int32), vp]
     L.btdf_batch_last_error.argtypes = [vp]
     L.btdf_batch_last_error.restype = C.c_char_p
     _lib = L
@@ -316,6 +318,15 @@ class Lattice:
         self._check(lib().btdf_device_bytes(self._ctx, C.byref(n)), "btdf_device_bytes")
         return n.value
 
+    def autotune(self, steps=20, flush_l2=True):
+        """Times every collide-stream variant on this lattice (btdf_autotune),
+        keeps the fastest; returns (chosen, {variant: median ms per step})."""
+        ch = C.c_int32()
+        ms = np.zeros(8, dtype=np.float32)
+        self._check(lib().btdf_autotune(self._ctx, int(steps), 1 if flush_l2 else 0, C.byref(ch),
+                                        ms.ctypes.data), "btdf_autotune")
+        return ch.value, {v: float(ms[v]) for v in range(1, 8) if ms[v] >= 0}
+
     def set_inflow(self, u_in):
         self._check(lib().btdf_set_inflow(self._ctx, float(u_in)), "btdf_set_inflow")
 
@@ -374,6 +385,7 @@ class Batch:
             raise BtdfError(rc, f"btdf_batch_create: {btdf_status_string(rc)}")
         self._b = out.value
         self.cases = list(cases)
+        self.storage = int(storage)
         self.bodies = []          # (lattice, markers) per batch-wide body id
 
     @classmethod
@@ -421,6 +433,14 @@ class Batch:
 
     def tune(self, variant):
         self._check(lib().btdf_batch_tune(self._b, int(variant)), "btdf_batch_tune")
+
+    def autotune(self, steps=10, flush_l2=False):
+        """Times launch shapes 1 and 2 on the batch (btdf_batch_autotune)."""
+        ch = C.c_int32()
+        ms = np.zeros(3, dtype=np.float32)
+        self._check(lib().btdf_batch_autotune(self._b, int(steps), 1 if flush_l2 else 0,
+                                              C.byref(ch), ms.ctypes.data), "btdf_batch_autotune")
+        return ch.value, {v: float(ms[v]) for v in (1, 2)}
 
     def step(self, n=1):
         self._check(lib().btdf_batch_step(self._b, int(n)), "btdf_batch_step")

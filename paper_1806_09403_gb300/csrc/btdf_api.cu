@@ -17,6 +17,37 @@
 #include <string>
 #include <vector>
 
+namespace btdf {
+namespace {
+
+__global__ void l2_read_kernel(const float4* __restrict__ buf, size_t n, float* __restrict__ sink) {
+    float acc = 0.f;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float4 v = buf[i];
+        acc += (v.x + v.y) + (v.z + v.w);
+    }
+    if (acc != 0.f) sink[0] = acc;   // the buffer is zero: never taken, keeps the loads live
+}
+
+}  // namespace
+
+cudaError_t launch_l2_flush(void* buf, size_t bytes, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(buf, 0, bytes, st);
+    if (e != cudaSuccess) return e;
+    const size_t n = bytes / sizeof(float4) - 1;   // the last float4 is the sink
+    l2_read_kernel<<<1024, kThreads, 0, st>>>((const float4*)buf, n, (float*)buf + 4 * n);
+    return cudaGetLastError();
+}
+
+size_t l2_flush_bytes() {
+    int dev = 0, l2 = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess)
+        l2 = 128 << 20;
+    return (size_t)std::max(l2, 1 << 20) * 4;
+}
+
+}  // namespace btdf
+
 using namespace btdf;
 
 namespace {
@@ -130,6 +161,7 @@ struct btdf_ctx {
     double u_ref = 0.0;
     std::vector<int> band_keys;        // y * nseg + segment of each band segment
     AdjointTape tape;
+    double2* tune_hist = nullptr;      // one-slot force ring used while btdf_autotune times steps
 };
 
 namespace {
@@ -259,6 +291,10 @@ LatticeParams lattice_params(const btdf_ctx* ctx) {
     p.body_ptr = ctx->d_body_ptr;
     p.body_scale = ctx->d_body_scale;
     p.hist = ctx->d_hist;
+    if (ctx->tune_hist) {   // timing steps must not overwrite the force history
+        p.hist_len = 1;
+        p.hist = ctx->tune_hist;
+    }
     return p;
 }
 
@@ -1151,6 +1187,117 @@ int btdf_adjoint_release(btdf_ctx* ctx) {
     CK(cudaStreamSynchronize(ctx->stream));
     free_tape(ctx);
     return BTDF_OK;
+}
+
+int btdf_autotune(btdf_ctx* ctx, int32_t steps, int32_t flush_l2, int32_t* chosen, float* ms) {
+    if (!ctx) return BTDF_EINVAL;
+    if (!ctx->has_fields) return fail(ctx, BTDF_ESTATE, "call btdf_init_fields or btdf_load_state first");
+    if (steps < 1 || steps > 100000) return fail(ctx, BTDF_EINVAL, "need 1 <= steps <= 100000");
+    cudaStream_t st = ctx->stream;
+    CK(cudaStreamSynchronize(st));
+    const int rc0 = read_status(ctx);
+    if (rc0 != BTDF_OK) return rc0;
+    // save what the timing steps change
+    const int cur0 = ctx->cur, var0 = ctx->variant;
+    const bool post0 = ctx->poststream;
+    const int64_t steps0 = ctx->steps;
+    unsigned long long counter0 = 0;
+    const size_t pbytes = (size_t)9 * ctx->plane * ctx->elem;
+    const size_t fbytes = sizeof(float2) * (size_t)ctx->nmark;
+    void* save = nullptr;
+    void* flush = nullptr;
+    double2* th = nullptr;
+    float2* fsave = nullptr;
+    const size_t nb = std::max<size_t>(ctx->bodies.size(), 1);
+    std::vector<cudaEvent_t> ev;
+    float res[kVarCount];
+    for (int v = 0; v < kVarCount; v++) res[v] = -1.0f;
+    int best = kVarReg4;
+    auto run = [&]() -> int {
+        CK(cudaMalloc(&save, pbytes));
+        CK(cudaMalloc((void**)&th, sizeof(double2) * nb));
+        if (fbytes) CK(cudaMalloc((void**)&fsave, 4 * fbytes));
+        if (flush_l2) CK(cudaMalloc(&flush, l2_flush_bytes()));
+        CK(cudaMemcpyAsync(&counter0, ctx->d_step, sizeof(counter0), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(save, ctx->g[cur0], pbytes, cudaMemcpyDeviceToDevice, st));
+        if (fbytes) {
+            CK(cudaMemcpyAsync(fsave, ctx->d_F[0], fbytes, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(fsave + ctx->nmark, ctx->d_F[1], fbytes, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(fsave + 2 * ctx->nmark, ctx->d_Us, fbytes, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(fsave + 3 * ctx->nmark, ctx->d_rhol, sizeof(float) * ctx->nmark,
+                               cudaMemcpyDeviceToDevice, st));
+        }
+        ctx->tune_hist = th;
+        ev.resize(2 * (size_t)steps);
+        for (auto& e : ev) CK(cudaEventCreate(&e));
+        if (ctx->poststream) {   // time pull steps only
+            int rc = enqueue_step(ctx, st, false, ctx->cur, false);
+            if (rc != BTDF_OK) return rc;
+            ctx->cur = 1 - ctx->cur;
+            ctx->poststream = false;
+        }
+        float best_ms = 0.f;
+        for (int v = 1; v < kVarCount; v++) {
+            if (is_tma(v) && !ctx->tma_ok) continue;
+            ctx->variant = v;
+            for (int i = 0; i < 3; i++) {
+                int rc = enqueue_step(ctx, st, true, ctx->cur, false);
+                if (rc != BTDF_OK) return rc;
+                ctx->cur = 1 - ctx->cur;
+            }
+            for (int i = 0; i < steps; i++) {
+                if (flush) CK(launch_l2_flush(flush, l2_flush_bytes(), st));
+                CK(cudaEventRecord(ev[2 * i], st));
+                int rc = enqueue_step(ctx, st, true, ctx->cur, false);
+                if (rc != BTDF_OK) return rc;
+                CK(cudaEventRecord(ev[2 * i + 1], st));
+                ctx->cur = 1 - ctx->cur;
+            }
+            CK(cudaStreamSynchronize(st));
+            std::vector<float> t(steps);
+            for (int i = 0; i < steps; i++) CK(cudaEventElapsedTime(&t[i], ev[2 * i], ev[2 * i + 1]));
+            std::sort(t.begin(), t.end());
+            res[v] = t[steps / 2];
+            if (v == 1 || res[v] < best_ms) {
+                best_ms = res[v];
+                best = v;
+            }
+        }
+        return BTDF_OK;
+    };
+    int rc = run();
+    // restore the state, the counter and the last step's marker results
+    ctx->tune_hist = nullptr;
+    ctx->variant = rc == BTDF_OK ? best : var0;
+    ctx->cur = cur0;
+    ctx->poststream = post0;
+    ctx->steps = steps0;
+    cudaError_t e = cudaSuccess;
+    if (save) {
+        e = cudaMemcpyAsync(ctx->g[cur0], save, pbytes, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->d_step, &counter0, sizeof(counter0), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && fsave) {
+            cudaMemcpyAsync(ctx->d_F[0], fsave, fbytes, cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync(ctx->d_F[1], fsave + ctx->nmark, fbytes, cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync(ctx->d_Us, fsave + 2 * ctx->nmark, fbytes, cudaMemcpyDeviceToDevice, st);
+            e = cudaMemcpyAsync(ctx->d_rhol, fsave + 3 * ctx->nmark, sizeof(float) * ctx->nmark,
+                                cudaMemcpyDeviceToDevice, st);
+        }
+    }
+    cudaStreamSynchronize(st);
+    for (auto& ev1 : ev)
+        if (ev1) cudaEventDestroy(ev1);
+    if (save) cudaFree(save);
+    if (flush) cudaFree(flush);
+    if (th) cudaFree(th);
+    if (fsave) cudaFree(fsave);
+    drop_graphs(ctx);
+    if (rc != BTDF_OK) return rc;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "restoring the state after tuning");
+    if (chosen) *chosen = best;
+    if (ms)
+        for (int v = 0; v < kVarCount; v++) ms[v] = res[v];
+    return read_status(ctx);
 }
 
 int btdf_device_bytes(const btdf_ctx* ctx, size_t* bytes) {

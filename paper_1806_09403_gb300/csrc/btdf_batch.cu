@@ -69,6 +69,7 @@ struct btdf_batch {
     std::vector<LatticeParams> descs;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     std::string err;
+    double2* tune_hist = nullptr;          // one-slot force ring while btdf_batch_autotune times steps
 };
 
 namespace {
@@ -311,6 +312,10 @@ BatchLbm lbm_params(const btdf_batch* bt, int s) {
     b.body_rng = bt->d_body_ptr;
     b.body_scale = bt->d_body_scale;
     b.hist = bt->d_hist;
+    if (bt->tune_hist) {   // timing steps must not overwrite the force history
+        b.hist_len = 1;
+        b.hist = bt->tune_hist;
+    }
     b.F = bt->d_F;
     b.step = bt->d_step;
     b.done = bt->d_done;
@@ -560,6 +565,96 @@ int btdf_batch_tune(btdf_batch* bt, int32_t variant) {
     drop_graphs(bt);
     bt->variant = variant == 2 ? 2 : 1;
     return BTDF_OK;
+}
+
+int btdf_batch_autotune(btdf_batch* bt, int32_t steps, int32_t flush_l2, int32_t* chosen, float* ms) {
+    if (!bt) return BTDF_EINVAL;
+    if (steps < 1 || steps > 100000) return bfail(bt, BTDF_EINVAL, "need 1 <= steps <= 100000");
+    for (int c = 0; c < bt->n; c++)
+        if (!bt->has_fields[c]) return bfail(bt, BTDF_ESTATE, "every lattice needs btdf_batch_init_fields");
+    cudaStream_t st = bt->stream;
+    BCK(cudaStreamSynchronize(st));
+    const int rc0 = bstatus(bt);
+    if (rc0 != BTDF_OK) return rc0;
+    const int cur0 = bt->cur, var0 = bt->variant;
+    const bool post0 = bt->poststream;
+    unsigned long long counter0 = 0;
+    const size_t pbytes = (size_t)9 * bt->total * bt->elem;
+    const size_t fbytes = sizeof(float2) * (size_t)bt->nmark;
+    void* save = nullptr;
+    void* flush = nullptr;
+    double2* th = nullptr;
+    float2* fsave = nullptr;
+    std::vector<cudaEvent_t> ev;
+    float res[3] = {-1.0f, -1.0f, -1.0f};
+    int best = 1;
+    auto run = [&]() -> int {
+        BCK(cudaMalloc(&save, pbytes));
+        BCK(cudaMalloc((void**)&th, sizeof(double2) * std::max<size_t>(bt->bodies.size(), 1)));
+        if (fbytes) BCK(cudaMalloc((void**)&fsave, fbytes));
+        if (flush_l2) BCK(cudaMalloc(&flush, l2_flush_bytes()));
+        BCK(cudaMemcpyAsync(&counter0, bt->d_step, sizeof(counter0), cudaMemcpyDeviceToHost, st));
+        BCK(cudaMemcpyAsync(save, bt->g[cur0], pbytes, cudaMemcpyDeviceToDevice, st));
+        if (fbytes) BCK(cudaMemcpyAsync(fsave, bt->d_F, fbytes, cudaMemcpyDeviceToDevice, st));
+        bt->tune_hist = th;
+        ev.resize(2 * (size_t)steps);
+        for (auto& e : ev) BCK(cudaEventCreate(&e));
+        if (bt->poststream) {   // time pull steps only
+            const int rc = enqueue(bt, st, false, bt->cur);
+            if (rc != BTDF_OK) return rc;
+            bt->cur = 1 - bt->cur;
+            bt->poststream = false;
+        }
+        for (int v = 1; v <= 2; v++) {
+            bt->variant = v;
+            for (int i = 0; i < 3; i++) {
+                const int rc = enqueue(bt, st, true, bt->cur);
+                if (rc != BTDF_OK) return rc;
+                bt->cur = 1 - bt->cur;
+            }
+            for (int i = 0; i < steps; i++) {
+                if (flush) BCK(launch_l2_flush(flush, l2_flush_bytes(), st));
+                BCK(cudaEventRecord(ev[2 * i], st));
+                const int rc = enqueue(bt, st, true, bt->cur);
+                if (rc != BTDF_OK) return rc;
+                BCK(cudaEventRecord(ev[2 * i + 1], st));
+                bt->cur = 1 - bt->cur;
+            }
+            BCK(cudaStreamSynchronize(st));
+            std::vector<float> t(steps);
+            for (int i = 0; i < steps; i++) BCK(cudaEventElapsedTime(&t[i], ev[2 * i], ev[2 * i + 1]));
+            std::sort(t.begin(), t.end());
+            res[v] = t[steps / 2];
+            if (v == 1 || res[v] < res[best]) best = v;
+        }
+        return BTDF_OK;
+    };
+    const int rc = run();
+    bt->tune_hist = nullptr;
+    bt->variant = rc == BTDF_OK ? best : var0;
+    bt->cur = cur0;
+    bt->poststream = post0;
+    cudaError_t e = cudaSuccess;
+    if (save) {
+        e = cudaMemcpyAsync(bt->g[cur0], save, pbytes, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(bt->d_step, &counter0, sizeof(counter0), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && fsave) e = cudaMemcpyAsync(bt->d_F, fsave, fbytes, cudaMemcpyDeviceToDevice, st);
+    }
+    cudaStreamSynchronize(st);
+    for (auto& ev1 : ev)
+        if (ev1) cudaEventDestroy(ev1);
+    if (save) cudaFree(save);
+    if (flush) cudaFree(flush);
+    if (th) cudaFree(th);
+    if (fsave) cudaFree(fsave);
+    drop_graphs(bt);
+    if (rc != BTDF_OK) return rc;
+    if (e != cudaSuccess) return bfail(bt, BTDF_ECUDA, "restoring the state after tuning");
+    if (chosen) *chosen = best;
+    if (ms)
+        for (int v = 0; v < 3; v++) ms[v] = res[v];
+    return bstatus(bt);
 }
 
 int btdf_batch_step(btdf_batch* bt, int64_t nsteps) {

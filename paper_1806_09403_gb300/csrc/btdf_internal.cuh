@@ -175,6 +175,12 @@ cudaError_t launch_init_equilibrium(int storage, void* g, const LatticeParams& p
 cudaError_t launch_read_field(int storage, bool pull, const void* g, const LatticeParams& p,
                               int kind, float* dst, cudaStream_t st);
 
+// Evicts the L2 cache before a timed launch (btdf_api.cu): writes `bytes`
+// of `buf`, then reads them back so the lines left behind are clean.
+cudaError_t launch_l2_flush(void* buf, size_t bytes, cudaStream_t st);
+// Bytes of scratch that evict the whole L2 of the current device.
+size_t l2_flush_bytes();
+
 // ---- discrete adjoint ----
 
 // Per-marker 1-D weights and their derivatives with respect to the marker

@@ -7,9 +7,13 @@ inflow speed U and every marker's radial offset dr_l.
 
 over the N steps that follow a fixed start state: the initial fields
 (window "init", N = 100, the first step reads the initial populations in
-place) or the state after 300 steps at the base parameters (window
-"spun_up", N = 500).  tau, ds and drs are held fixed.  eps = 1e-4; dJ/dU is
-also taken with 2 eps so that the truncation error can be checked.
+place) or the post-collision state after 300 steps at the base parameters
+(window "spun_up", N = 500).  In the second window the streaming that
+follows that state, inlet rule included, belongs to the window: the oracle
+holds post-streaming populations, so the inlet column of the loaded state
+is re-derived with the perturbed U before stepping.  tau, ds and drs are
+held fixed.  eps = 1e-4; dJ/dU is also taken with 2 eps so that the
+truncation error can be checked.
 
 Only the oracle and the seeded input generators are used.  Run from the
 repository root:  python tests/golden/make_adjoint_fd.py
@@ -56,6 +60,7 @@ def window_J(case, u, dr, start, nsteps):
     s.init_fields(rho, ux, uy)
     if start is not None:
         s.set_pops(start)
+        s.apply_inlet()
     r = R + np.asarray(dr)
     s.add_body(cx + r * np.cos(theta), cy + r * np.sin(theta), ds, drs=case.drs)
     s.step(nsteps)

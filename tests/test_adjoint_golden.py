@@ -67,3 +67,25 @@ def test_inflow_sensitivity_includes_inlet_path(name):
     norm_only = -2.0 * w["J"] / GOLD["u_in"]
     assert abs(w["dJdU"] - norm_only) > 1e-2 * abs(norm_only)
     assert abs(w["dJdU_2eps"] / w["dJdU"] - 1.0) < 1e-4
+
+
+def test_apply_inlet_is_the_inlet_rule_of_the_step():
+    """Re-applying the inlet rule to a state the same simulation just
+    streamed changes nothing; with another inlet speed only column 0 changes."""
+    O.build()
+    m = _maker()
+    case = m.base_case()
+    s = O.Sim.from_case(case)
+    s.step(20)
+    f = s.pops()
+    s.apply_inlet()
+    assert np.array_equal(s.pops(), f)
+    t = O.Sim(case.nx, case.ny, case.tau, case.u_in + 0.01, case.bc_x, case.bc_y, 0.0, 0.0,
+              case.delta, case.nf)
+    t.set_pops(f)
+    t.apply_inlet()
+    g = t.pops()
+    assert np.array_equal(g[:, 1:], f[:, 1:]) and not np.array_equal(g[:, 0], f[:, 0])
+    _, ux, _ = t.moments()
+    assert np.allclose(ux[:, 0], case.u_in + 0.01, rtol=0, atol=1e-12)
+

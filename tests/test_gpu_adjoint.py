@@ -13,11 +13,11 @@ the radial offsets dr_l of the markers.
   steps with a checkpoint every 50.  Bar: 1e-3 relative, for dJ/dU, for the
   vector dJ/d dr (norm-wise) and for each component against the largest.
 * 800 x 400 cylinder (D = 24, 76 markers, Re = 100, 3-point delta), 500-step
-  window with a checkpoint every 50: the adjoint against central differences
-  of the FP32 forward itself.  FP32 rounding makes those differences noisy
-  (the window mean of Cd carries ~1e-7 relative noise that eps = 1e-4
-  amplifies), so this comparison is indicative and its bar is looser; a
-  larger step (1e-2) is reported too.
+  window after 2000 steps with a checkpoint every 50: the adjoint against
+  central differences of the FP32 forward itself, for U and for the radial
+  offsets along one random direction.  FP32 rounding makes those differences
+  noisy where the step changes J by only a few ulps, so this comparison is
+  indicative; a larger step is reported beside eps = 1e-4.
 * The gradients do not depend on the checkpoint spacing.
 """
 import json
@@ -137,13 +137,18 @@ def test_adjoint_800x400_against_fp32_finite_differences():
     dU, g = win.gradients(case.u_in, z)
     v = np.random.default_rng(11).standard_normal(n)
     dirn = float(g @ v)
-    out = {}
-    for eps in (1e-4, 1e-2):
+    eU, ev = {}, {}
+    for eps in (1e-4, 1e-3):
         fdU = (win.evaluate(case.u_in + eps, z) - win.evaluate(case.u_in - eps, z)) / (2 * eps)
+        eU[eps] = rel(dU, fdU)
+        print(f"\n[800x400] J {J0:.6f}; dJ/dU adjoint {dU:.6e}, FD eps {eps:g} {fdU:.6e} ({eU[eps]:.1e})")
+    for eps in (1e-4, 1e-2):
         fdv = (win.evaluate(case.u_in, eps * v) - win.evaluate(case.u_in, -eps * v)) / (2 * eps)
-        out[eps] = (rel(dU, fdU), rel(dirn, fdv))
-        print(f"\n[800x400, eps {eps:g}] J {J0:.6f}; dJ/dU adjoint {dU:.6e} FD {fdU:.6e} "
-              f"({out[eps][0]:.1e}); along a random dr direction adjoint {dirn:.6e} "
-              f"FD {fdv:.6e} ({out[eps][1]:.1e})")
-    assert out[1e-2][0] <= 1e-2 and out[1e-2][1] <= 1e-2
-    assert out[1e-4][0] <= 5e-2 and out[1e-4][1] <= 5e-2
+        ev[eps] = rel(dirn, fdv)
+        print(f"[800x400] dJ/d dr along a random direction: adjoint {dirn:.6e}, FD eps {eps:g} "
+              f"{fdv:.6e} ({ev[eps]:.1e})")
+    # eps = 1e-4 in U changes J by ~6e-3 relative: well above FP32 noise
+    assert eU[1e-4] <= TOL
+    # a marker offset of 1e-4 changes J by ~1e-5 relative, ~100 FP32 ulps:
+    # the difference quotient carries ~1e-3 noise, so the larger step decides
+    assert ev[1e-2] <= 5e-3 and ev[1e-4] <= 2e-2
