@@ -579,7 +579,7 @@ int btdf_batch_autotune(btdf_batch* bt, int32_t steps, int32_t flush_l2, int32_t
     const int cur0 = bt->cur, var0 = bt->variant;
     const bool post0 = bt->poststream;
     unsigned long long counter0 = 0;
-    const size_t pbytes = (size_t)9 * bt->total * bt->elem;
+    const size_t pbytes = (size_t)bt->total * bt->elem;   // total counts all nine planes
     const size_t fbytes = sizeof(float2) * (size_t)bt->nmark;
     void* save = nullptr;
     void* flush = nullptr;
