@@ -166,6 +166,24 @@ def dist_setup(args):
     return world, rank, local
 
 
+def max_over_ranks(x, world, device="cuda"):
+    """The largest value of x over all ranks (the whole job ends with its
+    slowest replica); x itself with one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, seconds):
+    """Whole-job throughput of `world` replicas that each processed
+    units_per_rank units, timed by the slowest one."""
+    return units_per_rank * world / seconds
+
+
 def reference_arm(args):
     """FP64 CPU oracle on the host cores, same workload and metric.  Each step
     is one full oracle step of the lattice; the arm stops early once
@@ -383,7 +401,8 @@ def our_arm(args):
 
     # ---- kernel variant: the library's autotuner times each candidate on
     # this lattice (L2 evicted before every step, median of 32 steps) ----
-    names = {1: "reg4", 2: "reg2", 3: "tma8x2", 4: "tma8x3", 5: "tma16x2", 6: "reg4pf", 7: "reg2pf"}
+    names = {1: "reg4", 2: "reg2", 3: "tma8x2", 4: "tma8x3", 5: "tma16x2", 6: "reg4pf", 7: "reg2pf",
+             8: "reg1", 9: "reg2o"}
     if args.variant == 0:
         best, tms = lat.autotune(32, True)
         tune = {names[v]: t for v, t in tms.items()}
@@ -403,13 +422,8 @@ def our_arm(args):
             lat.step(1)
             ev[i][1].record(stream)
         barrier()
-    ms = sum(a.elapsed_time(b) for a, b in ev)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = nodes * args.steps * world / (ms / 1e3) / 1e6
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world)
+    value = job_rate(nodes * args.steps, world, ms / 1e3) / 1e6
 
     # ---- per-kernel durations (library events around each kernel, no overlap) ----
     lat.profile(True)
@@ -462,12 +476,8 @@ def our_arm(args):
         else:
             lat.sync()
         tot += time.perf_counter() - t0
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([tot], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot = float(t.item())
-    e2e = nodes * ne2e * world / tot / 1e6
+    tot = max_over_ranks(tot, world)
+    e2e = job_rate(nodes * ne2e, world, tot) / 1e6
 
     # ---- FP64 oracle on the host cores, and drag error against it ----
     cpu = None
@@ -535,7 +545,7 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=90.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="bench", choices=["bench", "kernel", "batch", "adjoint"])
-    ap.add_argument("--variant", type=int, default=0, choices=list(range(8)))
+    ap.add_argument("--variant", type=int, default=0, choices=list(range(10)))
     ap.add_argument("--layout", default="rows", choices=["rows", "planes"])
     args = ap.parse_args()
     if args.warmup < 3:

@@ -137,7 +137,10 @@ int btdf_add_markers(btdf_ctx *ctx, int32_t n, const double *X, const double *Y,
                      int32_t *body_id);
 
 /* Replaces the prescribed marker velocities U_b of one body (host arrays of
- * that body's marker count).  Asynchronous on the context stream. */
+ * that body's marker count, read before the call returns).  The upload is
+ * asynchronous on the context stream through one of four page-locked
+ * staging slots; a call waits only when the upload four calls back has not
+ * run yet. */
 int btdf_set_marker_velocity(btdf_ctx *ctx, int32_t body, const double *Ubx, const double *Uby);
 
 /* Changes the inlet speed of BTDF_BCX_INOUT (the non-equilibrium
@@ -167,6 +170,14 @@ int btdf_sync(btdf_ctx *ctx);
  * Synchronizes.  Errors: EINVAL (body or step range). */
 int btdf_read_forces(btdf_ctx *ctx, int32_t body, int64_t first, int64_t n,
                      double *Fx, double *Fy);
+
+/* As btdf_read_forces, without waiting: enqueues the copy of the steps
+ * first .. first+n-1 into F[2 i] = Fx, F[2 i + 1] = Fy on the context
+ * stream and returns.  F must stay valid until the stream reaches the copy
+ * (btdf_sync); page-locked memory (cudaMallocHost, a pinned torch tensor)
+ * makes it a DMA transfer that overlaps host work, pageable memory makes
+ * the call wait for the copy.  Device status is reported by btdf_sync. */
+int btdf_read_forces_async(btdf_ctx *ctx, int32_t body, int64_t first, int64_t n, double *F);
 
 /* Per-marker results of the last step for one body, host arrays of the body's
  * marker count (any may be NULL): interpolated unforced velocity D_I u*
@@ -200,7 +211,7 @@ int btdf_profile_read(btdf_ctx *ctx, double *ms_ib, double *ms_lbm, int64_t *lau
                       int64_t *launches_lbm);
 
 /* Variant of the fused collide-stream kernel.  Results do not depend on it.
- *   0 automatic (3 when tensor maps are available, else 1)
+ *   0 automatic (2 for FP32 storage, 1 for FP16 / BF16)
  *   1 register-pipelined warps, 4 nodes per lane (16-byte FP32 vectors)
  *   2 register-pipelined warps, 2 nodes per lane
  *   3 TMA-tiled CTAs: 128 x 8 node tiles, 2 pipeline stages
@@ -208,8 +219,12 @@ int btdf_profile_read(btdf_ctx *ctx, double *ms_ib, double *ms_lbm, int64_t *lau
  *   5 TMA-tiled CTAs: 128 x 16 node tiles, 2 pipeline stages
  *   6 register warps, 4 nodes per lane, next segment's loads issued early
  *   7 register warps, 2 nodes per lane, next segment's loads issued early
- * grid_blocks caps the persistent grid (0 = SM count x resident blocks per
- * SM).  Synchronizes and drops cached CUDA graphs.
+ *   8 register warps, 1 node per lane, 6 resident blocks per SM
+ *   9 register warps, 2 nodes per lane, 5 resident blocks per SM
+ * grid_blocks caps the grid (0 = default: one 32 x NPL-node row segment per
+ * warp for variants 1, 2, 8 and 9, so the block scheduler balances the SMs;
+ * SM count x resident blocks per SM for the persistent variants 3-7).
+ * Synchronizes and drops cached CUDA graphs.
  * Errors: EINVAL (unknown variant, TMA variant without tensor maps). */
 int btdf_tune(btdf_ctx *ctx, int32_t variant, int32_t grid_blocks);
 
@@ -217,7 +232,7 @@ int btdf_tune(btdf_ctx *ctx, int32_t variant, int32_t grid_blocks);
 int btdf_device_bytes(const btdf_ctx *ctx, size_t *bytes);
 
 /* Autotuner of the collide-stream launch: times every available variant of
- * btdf_tune (1..7; the TMA variants only where tensor maps were encoded) on
+ * btdf_tune (1..9; the TMA variants only where tensor maps were encoded) on
  * this context's own lattice, `steps` steps each after 3 untimed ones, every
  * step (IB and LBM stage, overlapped as in btdf_step) between CUDA events on
  * the context stream, with the L2 cache evicted before each step when
@@ -225,7 +240,7 @@ int btdf_device_bytes(const btdf_ctx *ctx, size_t *bytes);
  * populations, the step counter, the force history and the last step's
  * marker results are restored afterwards, so the simulation does not
  * advance.  Outputs (may be NULL): *chosen, and ms[v] = median ms per step of
- * variant v for v = 0..7 (-1 where not timed).  Needs temporary device memory
+ * variant v for v = 0..9 (-1 where not timed).  Needs temporary device memory
  * for one copy of the populations and, with flush_l2, four times the L2 size.
  * Synchronizes.  Errors: EINVAL (steps outside 1..100000), ESTATE (no fields),
  * ENOMEM / ECUDA. */
@@ -291,9 +306,11 @@ int btdf_batch_add_markers(btdf_batch *b, int32_t lattice, int32_t n, const doub
 int btdf_batch_body_count(const btdf_batch *b, int32_t *n);
 int btdf_batch_body_lattice(const btdf_batch *b, int32_t body, int32_t *lattice);
 /* Collide-stream launch shape: 1 = 4 nodes per lane, 2 = 2 nodes per lane,
- * 0 = default (1).  Results do not depend on it. */
+ * on a persistent grid whose CTAs own balanced ranges of 8-row units;
+ * 3 = 4, 4 = 2 nodes per lane with one unit per CTA (the block scheduler
+ * balances the SMs); 0 = default (1).  Results do not depend on it. */
 int btdf_batch_tune(btdf_batch *b, int32_t variant);
-/* As btdf_autotune, over the batch's launch shapes 1 and 2; ms[0..2]. */
+/* As btdf_autotune, over the batch's launch shapes 1..4; ms[0..4]. */
 int btdf_batch_autotune(btdf_batch *b, int32_t steps, int32_t flush_l2, int32_t *chosen, float *ms);
 int btdf_batch_step(btdf_batch *b, int64_t nsteps);
 int btdf_batch_sync(btdf_batch *b);

@@ -38,8 +38,10 @@ EXPORTS = [
     "btdf_batch_sync", "btdf_batch_step_count", "btdf_batch_read_forces", "btdf_batch_read_field",
     "btdf_batch_last_error", "btdf_set_inflow", "btdf_move_markers", "btdf_adjoint_forward",
     "btdf_adjoint_backward", "btdf_adjoint_release", "btdf_autotune", "btdf_batch_autotune",
+    "btdf_read_forces_async",
 ]
 STATIC_MAX_MARKERS = 2048
+VARIANT_COUNT = 10          # collide-stream variants 0 (automatic) .. 9, see btdf_tune
 STATE_HEADER_BYTES = 40
 
 
@@ -90,6 +92,7 @@ def lib() -> C.CDLL:
     L.btdf_sync.argtypes = [ctxp]
     L.btdf_read_forces.argtypes = [ctxp, C.c_int32, C.c_int64, C.c_int64, vp, vp]
     L.btdf_read_markers.argtypes = [ctxp, C.c_int32, vp, vp, vp, vp]
+    L.btdf_read_forces_async.argtypes = [ctxp, C.c_int32, C.c_int64, C.c_int64, vp]
     L.btdf_read_field.argtypes = [ctxp, C.c_int32, vp, C.c_int32]
     L.btdf_step_count.argtypes = [ctxp]
     L.btdf_step_count.restype = C.c_int64
@@ -268,6 +271,13 @@ class Lattice:
                                            Fy.ctypes.data), "btdf_read_forces")
         return Fx, Fy
 
+    def forces_async(self, body, first, n, ptr: int):
+        """Enqueues the copy of n steps' body force into host memory at ptr
+        (n x 2 doubles, Fx Fy; page-locked for a true asynchronous copy);
+        valid after sync()."""
+        self._check(lib().btdf_read_forces_async(self._ctx, int(body), int(first), int(n), ptr),
+                    "btdf_read_forces_async")
+
     def markers(self, body=0):
         n = self.body_markers[body]
         a = [np.zeros(n, dtype=np.float32) for _ in range(4)]
@@ -322,10 +332,10 @@ class Lattice:
         """Times every collide-stream variant on this lattice (btdf_autotune),
         keeps the fastest; returns (chosen, {variant: median ms per step})."""
         ch = C.c_int32()
-        ms = np.zeros(8, dtype=np.float32)
+        ms = np.zeros(VARIANT_COUNT, dtype=np.float32)
         self._check(lib().btdf_autotune(self._ctx, int(steps), 1 if flush_l2 else 0, C.byref(ch),
                                         ms.ctypes.data), "btdf_autotune")
-        return ch.value, {v: float(ms[v]) for v in range(1, 8) if ms[v] >= 0}
+        return ch.value, {v: float(ms[v]) for v in range(1, VARIANT_COUNT) if ms[v] >= 0}
 
     def set_inflow(self, u_in):
         self._check(lib().btdf_set_inflow(self._ctx, float(u_in)), "btdf_set_inflow")
@@ -435,12 +445,12 @@ class Batch:
         self._check(lib().btdf_batch_tune(self._b, int(variant)), "btdf_batch_tune")
 
     def autotune(self, steps=10, flush_l2=False):
-        """Times launch shapes 1 and 2 on the batch (btdf_batch_autotune)."""
+        """Times launch shapes 1..4 on the batch (btdf_batch_autotune)."""
         ch = C.c_int32()
-        ms = np.zeros(3, dtype=np.float32)
+        ms = np.zeros(5, dtype=np.float32)
         self._check(lib().btdf_batch_autotune(self._b, int(steps), 1 if flush_l2 else 0,
                                               C.byref(ch), ms.ctypes.data), "btdf_batch_autotune")
-        return ch.value, {v: float(ms[v]) for v in (1, 2)}
+        return ch.value, {v: float(ms[v]) for v in (1, 2, 3, 4)}
 
     def step(self, n=1):
         self._check(lib().btdf_batch_step(self._b, int(n)), "btdf_batch_step")

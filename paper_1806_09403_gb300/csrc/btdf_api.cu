@@ -53,6 +53,8 @@ using namespace btdf;
 namespace {
 
 constexpr int kGraphSteps = 64;          // steps per replayed CUDA graph (even)
+constexpr int kFullGrid = 1 << 30;       // grid cap meaning "one row segment per warp"
+constexpr int kStageSlots = 4;           // pinned staging slots for marker velocities
 constexpr uint64_t kStateMagic = 0x3130465444544242ull;
 
 struct Body {
@@ -138,9 +140,19 @@ struct btdf_ctx {
     unsigned long long* d_step = nullptr;
     int* d_status = nullptr;
     std::vector<MarkerAux> aux_host;
+    // Pinned host staging, so per-step host <-> device copies are true DMA
+    // transfers and a step's inputs and outputs need one synchronization.
+    // kStageSlots x [nmark] marker velocities on their way to the device;
+    // slot k is reused once its upload (aux_ev[k]) has run, so the host can
+    // prepare a few steps ahead of the device.
+    MarkerAux* aux_pin = nullptr;
+    cudaEvent_t aux_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    int aux_slot = 0;
+    int* status_pin = nullptr;         // device status word
+    void* pin = nullptr;               // force-history read-back
+    size_t pin_cap = 0;
 
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-    long long lbm_grid[2][2] = {{1, 1}, {1, 1}};   // persistent LBM grid [npl 4/2][local/pull]
     long long pf_grid[2] = {1, 1};                 // software-pipelined kernel [npl 4/2]
     long long tma_grid[kVarCount] = {};  // persistent grid of each TMA variant
     int variant = kVarAuto;              // LBM kernel variant (btdf_tune)
@@ -207,6 +219,10 @@ void drop_graphs(btdf_ctx* ctx) {
 }
 
 void free_markers(btdf_ctx* ctx) {
+    for (cudaEvent_t e : ctx->aux_ev)
+        if (e) cudaEventSynchronize(e);
+    if (ctx->aux_pin) cudaFreeHost(ctx->aux_pin);
+    ctx->aux_pin = nullptr;
     ctx->dev_bytes -= ctx->marker_bytes;
     ctx->marker_bytes = 0;
     dfree(ctx, ctx->d_mk);
@@ -338,23 +354,24 @@ int enqueue_step(btdf_ctx* ctx, cudaStream_t st, bool pull, int cur, bool prof) 
     // dependent of the IB kernel: its band nodes wait for the forces, the rest
     // of the lattice overlaps the IB stage.
     const bool pdl = ctx->nmark > 0 && !prof;
-    int v = ctx->variant == kVarAuto ? (ctx->tma_ok ? kVarTma8x2 : kVarReg4) : ctx->variant;
+    int v = ctx->variant == kVarAuto ? (ctx->cfg.storage == kStoreF32 ? kVarReg2 : kVarReg4) : ctx->variant;
     if (is_tma(v) && (!pull || !ctx->tma_ok)) v = kVarReg4;   // TMA kernel pulls only
     if (is_tma(v)) {
         const int grid = ctx->grid_override > 0 ? ctx->grid_override : (int)ctx->tma_grid[v];
         CK(launch_collide_stream_tma(ctx->cfg.storage, v, &ctx->tmap[cur][v == kVarTma16x2 ? 1 : 0],
                                      ctx->g[cur], ctx->g[1 - cur], p, grid, pdl, st));
-    } else if ((v == kVarReg4Pf || v == kVarReg2Pf) && pull) {
-        const int npl = v == kVarReg2Pf ? 2 : 4;
-        const int grid = ctx->grid_override > 0 ? ctx->grid_override : (int)ctx->pf_grid[npl == 2 ? 1 : 0];
-        CK(launch_collide_stream(ctx->cfg.storage, true, -npl, ctx->g[cur], ctx->g[1 - cur], p, grid,
-                                 pdl, st));
     } else {
-        const int npl = (v == kVarReg2 || v == kVarReg2Pf) ? 2 : 4;
+        // Register variants.  Default grid: one row segment per warp.  SMs
+        // stream at different rates (per-SM busy time spreads by +-20% at
+        // equal work), and a grid the block scheduler hands out as SMs free
+        // up balances them; measured 0.39 ms against 0.53 ms per step of the
+        // persistent grid on an 8192 x 4096 lattice.  The software-pipelined
+        // variants are persistent by design.
+        const bool pf = (v == kVarReg4Pf || v == kVarReg2Pf) && pull;
         const int grid = ctx->grid_override > 0 ? ctx->grid_override
-                                                : (int)ctx->lbm_grid[npl == 2 ? 1 : 0][pull ? 1 : 0];
-        CK(launch_collide_stream(ctx->cfg.storage, pull, npl, ctx->g[cur], ctx->g[1 - cur], p, grid,
-                                 pdl, st));
+                         : pf                   ? (int)ctx->pf_grid[v == kVarReg2Pf ? 1 : 0]
+                                                : kFullGrid;
+        CK(launch_collide_stream(ctx->cfg.storage, pull, v, ctx->g[cur], ctx->g[1 - cur], p, grid, pdl, st));
     }
     if (prof) CK(cudaEventRecord(e2, st));
     return BTDF_OK;
@@ -417,9 +434,9 @@ bool encode_tensor_maps(btdf_ctx* ctx) {
 }
 
 int read_status(btdf_ctx* ctx) {
-    int st = 0;
-    CK(cudaMemcpyAsync(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->status_pin, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    const int st = *ctx->status_pin;
     if (st & kStatusTimeout) return fail(ctx, BTDF_ETIMEOUT, "a bounded device wait gave up");
     if (st & kStatusUnstable)
         return fail(ctx, BTDF_EUNSTABLE, "non-positive or non-finite density or force at a marker");
@@ -457,6 +474,7 @@ int rebuild_markers(btdf_ctx* ctx) {
         B.wsum.assign(t.wsum.begin() + B.first, t.wsum.begin() + B.first + B.n);
     }
     ctx->aux_host = t.aux;
+    CK(cudaMallocHost((void**)&ctx->aux_pin, sizeof(MarkerAux) * nm * kStageSlots));
     ctx->nband = (int)t.seg_keys.size();
     const std::vector<Marker>& mk = t.mk;
     const std::vector<int>& seg_index = t.seg_index;
@@ -558,8 +576,7 @@ int tape_step(btdf_ctx* ctx, int64_t n, const float* gin, float* gout) {
     q.first_pass = 1;
     q.status = ctx->d_status;
     CK(launch_ib_force(kStoreF32, pull, ctx->width, gin, p, q, ctx->stream));
-    CK(launch_collide_stream(kStoreF32, pull, 4, gin, gout, p, (int)ctx->lbm_grid[0][pull ? 1 : 0], true,
-                             ctx->stream));
+    CK(launch_collide_stream(kStoreF32, pull, kVarReg4, gin, gout, p, kFullGrid, true, ctx->stream));
     return BTDF_OK;
 }
 
@@ -696,14 +713,10 @@ int btdf_create(const btdf_config* cfg, void* stream, btdf_ctx** out) {
         if (cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return bail(BTDF_ECUDA);
-        for (int v = 0; v < 2; v++)
-            for (int pull = 0; pull < 2; pull++)
-                ctx->lbm_grid[v][pull] =
-                    (long long)sms * collide_stream_blocks_per_sm(c.storage, pull != 0, v == 0 ? 4 : 2);
         for (int v = 0; v < kVarCount; v++)
             if (is_tma(v)) ctx->tma_grid[v] = (long long)sms * collide_stream_tma_blocks_per_sm(c.storage, v);
-        ctx->pf_grid[0] = (long long)sms * collide_stream_blocks_per_sm(c.storage, true, -4);
-        ctx->pf_grid[1] = (long long)sms * collide_stream_blocks_per_sm(c.storage, true, -2);
+        ctx->pf_grid[0] = (long long)sms * collide_stream_blocks_per_sm(c.storage, true, kVarReg4Pf);
+        ctx->pf_grid[1] = (long long)sms * collide_stream_blocks_per_sm(c.storage, true, kVarReg2Pf);
     }
     const size_t bytes = (size_t)9 * ctx->plane * ctx->elem;
     for (int i = 0; i < 2; i++) {
@@ -715,6 +728,10 @@ int btdf_create(const btdf_config* cfg, void* stream, btdf_ctx** out) {
     ctx->tma_ok = encode_tensor_maps(ctx);
     for (int v = 0; v < kVarCount; v++)
         if (is_tma(v) && ctx->tma_grid[v] <= 0) ctx->tma_ok = false;
+    if (cudaMallocHost((void**)&ctx->status_pin, sizeof(int)) != cudaSuccess) return bail(BTDF_ECUDA);
+    for (cudaEvent_t& e : ctx->aux_ev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return bail(BTDF_ECUDA);
+    *ctx->status_pin = 0;
     if (dalloc(ctx, &ctx->d_step, sizeof(unsigned long long)) != cudaSuccess ||
         dalloc(ctx, &ctx->d_status, sizeof(int)) != cudaSuccess)
         return bail(BTDF_ECUDA);
@@ -737,6 +754,10 @@ int btdf_destroy(btdf_ctx* ctx) {
     dfree(ctx, ctx->d_step);
     dfree(ctx, ctx->d_status);
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : ctx->aux_ev)
+        if (e) cudaEventDestroy(e);
+    if (ctx->status_pin) cudaFreeHost(ctx->status_pin);
+    if (ctx->pin) cudaFreeHost(ctx->pin);
     if (ctx->cap) cudaStreamDestroy(ctx->cap);
     delete ctx;
     return BTDF_OK;
@@ -816,18 +837,23 @@ int btdf_set_marker_velocity(btdf_ctx* ctx, int32_t body, const double* Ubx, con
     for (int l = 0; l < B.n; l++)
         if (!std::isfinite(Ubx[l]) || !std::isfinite(Uby[l]))
             return fail(ctx, BTDF_EINVAL, "marker velocity not finite");
+    // this staging slot may still feed an upload kStageSlots calls back
+    const int k = ctx->aux_slot;
+    ctx->aux_slot = (k + 1) % kStageSlots;
+    CK(cudaEventSynchronize(ctx->aux_ev[k]));
+    MarkerAux* stage = ctx->aux_pin + (size_t)k * ctx->nmark;
     for (int l = 0; l < B.n; l++) {
         B.Ubx[l] = Ubx[l];
         B.Uby[l] = Uby[l];
         MarkerAux& A = ctx->aux_host[B.first + l];
         A.ubx_rel = (float)(Ubx[l] - ctx->u_ref * B.wsum[l]);
         A.uby_rel = (float)Uby[l];
+        stage[B.first + l] = A;
     }
     ctx->tape.pending = false;
-    CK(cudaMemcpyAsync(ctx->d_aux + B.first, ctx->aux_host.data() + B.first, sizeof(MarkerAux) * B.n,
+    CK(cudaMemcpyAsync(ctx->d_aux + B.first, stage + B.first, sizeof(MarkerAux) * B.n,
                        cudaMemcpyHostToDevice, ctx->stream));
-    // the host copy may change again before the copy runs: make it complete
-    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaEventRecord(ctx->aux_ev[k], ctx->stream));
     return BTDF_OK;
 }
 
@@ -876,23 +902,52 @@ int btdf_read_forces(btdf_ctx* ctx, int32_t body, int64_t first, int64_t n, doub
     if (first < ctx->hist_from || first < ctx->steps - H || first + n > ctx->steps)
         return fail(ctx, BTDF_EINVAL, "requested steps are not in the force history");
     const int nb = (int)ctx->bodies.size();
-    std::vector<double2> tmp((size_t)n);
+    const size_t need = sizeof(double2) * (size_t)std::max<int64_t>(n, 1);
+    if (ctx->pin_cap < need) {
+        CK(cudaStreamSynchronize(ctx->stream));
+        if (ctx->pin) cudaFreeHost(ctx->pin);
+        ctx->pin = nullptr;
+        ctx->pin_cap = 0;
+        CK(cudaMallocHost(&ctx->pin, need));
+        ctx->pin_cap = need;
+    }
+    double2* tmp = (double2*)ctx->pin;
     int64_t done = 0;
     while (done < n) {
         const int64_t s = first + done;
         const int64_t slot = s % H;
         const int64_t cnt = std::min<int64_t>(n - done, H - slot);
-        CK(cudaMemcpy2DAsync(tmp.data() + done, sizeof(double2), ctx->d_hist + slot * nb + body,
+        CK(cudaMemcpy2DAsync(tmp + done, sizeof(double2), ctx->d_hist + slot * nb + body,
                              sizeof(double2) * nb, sizeof(double2), (size_t)cnt,
                              cudaMemcpyDeviceToHost, ctx->stream));
         done += cnt;
     }
-    const int rc = read_status(ctx);
+    const int rc = read_status(ctx);   // one synchronization for both copies
     for (int64_t i = 0; i < n; i++) {
         Fx[i] = tmp[i].x;
         Fy[i] = tmp[i].y;
     }
     return rc;
+}
+
+int btdf_read_forces_async(btdf_ctx* ctx, int32_t body, int64_t first, int64_t n, double* F) {
+    if (!ctx) return BTDF_EINVAL;
+    if (body < 0 || body >= (int)ctx->bodies.size() || n < 0 || (n > 0 && !F))
+        return fail(ctx, BTDF_EINVAL, "bad body index, count or null output");
+    const int64_t H = ctx->cfg.history_len;
+    if (first < ctx->hist_from || first < ctx->steps - H || first + n > ctx->steps)
+        return fail(ctx, BTDF_EINVAL, "requested steps are not in the force history");
+    const int nb = (int)ctx->bodies.size();
+    int64_t done = 0;
+    while (done < n) {
+        const int64_t slot = (first + done) % H;
+        const int64_t cnt = std::min<int64_t>(n - done, H - slot);
+        CK(cudaMemcpy2DAsync(F + 2 * done, sizeof(double2), ctx->d_hist + slot * nb + body,
+                             sizeof(double2) * nb, sizeof(double2), (size_t)cnt,
+                             cudaMemcpyDeviceToHost, ctx->stream));
+        done += cnt;
+    }
+    return BTDF_OK;
 }
 
 int btdf_read_markers(btdf_ctx* ctx, int32_t body, float* Usx, float* Usy, float* Fbx, float* Fby) {

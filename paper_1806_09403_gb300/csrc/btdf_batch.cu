@@ -41,7 +41,9 @@ struct btdf_batch {
     bool poststream = true;
     std::vector<char> has_fields;
     int64_t steps = 0, hist_from = 0;
-    int variant = 1;                       // 1: 4 nodes per lane, 2: 2 nodes per lane
+    // launch shape: 1 / 2 = 4 / 2 nodes per lane on a persistent grid of
+    // balanced unit ranges; 3 / 4 = the same with one unit per CTA
+    int variant = 1;
     int grid[2] = {1, 1};
     int sms = 1;
 
@@ -49,9 +51,9 @@ struct btdf_batch {
     int nmark = 0;
     LatticeParams* d_descs = nullptr;
     unsigned long long* d_off = nullptr;
-    int2* d_units[2] = {nullptr, nullptr};
-    int* d_cta[2] = {nullptr, nullptr};
-    int grid_used[2] = {1, 1};
+    int2* d_units[4] = {nullptr, nullptr, nullptr, nullptr};   // per launch shape
+    int* d_cta[4] = {nullptr, nullptr, nullptr, nullptr};
+    int grid_used[4] = {1, 1, 1, 1};
     Marker* d_mk = nullptr;
     MarkerAux* d_aux = nullptr;
     float2* d_F = nullptr;
@@ -153,8 +155,10 @@ LatticeParams base_params(const btdf_batch* bt, int c) {
 
 // Work units (lattice, first row) of 8 rows, and a split into `grid`
 // contiguous CTA ranges of nearly equal segment counts.
+int shape_npl(int v) { return (v == 2 || v == 4) ? 2 : 4; }
+
 int build_units(btdf_batch* bt, int v) {
-    const int npl = v == 2 ? 2 : 4, sw = 32 * npl;
+    const int npl = shape_npl(v), sw = 32 * npl;
     std::vector<int2> units;
     std::vector<long long> work;
     for (int c = 0; c < bt->n; c++) {
@@ -166,8 +170,8 @@ int build_units(btdf_batch* bt, int v) {
     }
     long long total = 0;
     for (long long w : work) total += w;
-    const int grid = (int)std::max<long long>(1, std::min<long long>(bt->grid[v == 2 ? 1 : 0],
-                                                                      (long long)units.size()));
+    const long long cap = v >= 3 ? (long long)units.size() : (long long)bt->grid[npl == 2 ? 1 : 0];
+    const int grid = (int)std::max<long long>(1, std::min<long long>(cap, (long long)units.size()));
     std::vector<int> cta(grid + 1, (int)units.size());
     cta[0] = 0;
     long long acc = 0;
@@ -177,7 +181,7 @@ int build_units(btdf_batch* bt, int v) {
         while (b < grid && acc * grid >= total * b) cta[b++] = (int)u + 1;
     }
     for (; b < grid; b++) cta[b] = (int)units.size();
-    const int s = v == 2 ? 1 : 0;
+    const int s = v - 1;
     bfree(bt->d_units[s]);
     bfree(bt->d_cta[s]);
     BCK(cudaMalloc((void**)&bt->d_units[s], sizeof(int2) * std::max<size_t>(units.size(), 1)));
@@ -336,8 +340,8 @@ int enqueue(btdf_batch* bt, cudaStream_t st, bool pull, int cur) {
         q.status = bt->d_status;
         BCK(launch_ib_force_batch(bt->storage, pull, bt->width, bt->g[cur], bt->d_descs, bt->d_off, q, st));
     }
-    const int s = bt->variant == 2 ? 1 : 0;
-    BCK(launch_collide_stream_batch(bt->storage, pull, bt->variant == 2 ? 2 : 4, bt->g[cur],
+    const int s = bt->variant - 1;
+    BCK(launch_collide_stream_batch(bt->storage, pull, shape_npl(bt->variant), bt->g[cur],
                                     bt->g[1 - cur], lbm_params(bt, s), bt->grid_used[s],
                                     bt->nmark > 0, st));
     return BTDF_OK;
@@ -458,7 +462,8 @@ int btdf_batch_create(const btdf_config* cfgs, int32_t n, void* stream, btdf_bat
         return bail(BTDF_ECUDA);
     bt->descs.resize(n);
     for (int c = 0; c < n; c++) bt->descs[c] = base_params(bt, c);
-    if (build_units(bt, 1) != BTDF_OK || build_units(bt, 2) != BTDF_OK || rebuild(bt) != BTDF_OK)
+    if (build_units(bt, 1) != BTDF_OK || build_units(bt, 2) != BTDF_OK || build_units(bt, 3) != BTDF_OK ||
+        build_units(bt, 4) != BTDF_OK || rebuild(bt) != BTDF_OK)
         return bail(BTDF_ECUDA);
     *out = bt;
     return BTDF_OK;
@@ -473,7 +478,7 @@ int btdf_batch_destroy(btdf_batch* bt) {
     bfree(bt->g[1]);
     bfree(bt->d_descs);
     bfree(bt->d_off);
-    for (int s = 0; s < 2; s++) {
+    for (int s = 0; s < 4; s++) {
         bfree(bt->d_units[s]);
         bfree(bt->d_cta[s]);
     }
@@ -560,10 +565,10 @@ int btdf_batch_body_lattice(const btdf_batch* bt, int32_t body, int32_t* lattice
 
 int btdf_batch_tune(btdf_batch* bt, int32_t variant) {
     if (!bt) return BTDF_EINVAL;
-    if (variant != 0 && variant != 1 && variant != 2) return bfail(bt, BTDF_EINVAL, "variant must be 0, 1 or 2");
+    if (variant < 0 || variant > 4) return bfail(bt, BTDF_EINVAL, "variant must be 0 .. 4");
     BCK(cudaStreamSynchronize(bt->stream));
     drop_graphs(bt);
-    bt->variant = variant == 2 ? 2 : 1;
+    bt->variant = variant == 0 ? 1 : variant;
     return BTDF_OK;
 }
 
@@ -586,7 +591,7 @@ int btdf_batch_autotune(btdf_batch* bt, int32_t steps, int32_t flush_l2, int32_t
     double2* th = nullptr;
     float2* fsave = nullptr;
     std::vector<cudaEvent_t> ev;
-    float res[3] = {-1.0f, -1.0f, -1.0f};
+    float res[5] = {-1.0f, -1.0f, -1.0f, -1.0f, -1.0f};
     int best = 1;
     auto run = [&]() -> int {
         BCK(cudaMalloc(&save, pbytes));
@@ -605,7 +610,7 @@ int btdf_batch_autotune(btdf_batch* bt, int32_t steps, int32_t flush_l2, int32_t
             bt->cur = 1 - bt->cur;
             bt->poststream = false;
         }
-        for (int v = 1; v <= 2; v++) {
+        for (int v = 1; v <= 4; v++) {
             bt->variant = v;
             for (int i = 0; i < 3; i++) {
                 const int rc = enqueue(bt, st, true, bt->cur);
@@ -653,7 +658,7 @@ int btdf_batch_autotune(btdf_batch* bt, int32_t steps, int32_t flush_l2, int32_t
     if (e != cudaSuccess) return bfail(bt, BTDF_ECUDA, "restoring the state after tuning");
     if (chosen) *chosen = best;
     if (ms)
-        for (int v = 0; v < 3; v++) ms[v] = res[v];
+        for (int v = 0; v < 5; v++) ms[v] = res[v];
     return bstatus(bt);
 }
 

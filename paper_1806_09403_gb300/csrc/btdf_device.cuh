@@ -22,6 +22,8 @@ template <> struct Io<float> {
         if constexpr (N == 4) {
             const float4 v = *reinterpret_cast<const float4*>(p);
             o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+        } else if constexpr (N == 1) {
+            o[0] = *p;
         } else {
             const float2 v = *reinterpret_cast<const float2*>(p);
             o[0] = v.x; o[1] = v.y;
@@ -30,6 +32,7 @@ template <> struct Io<float> {
     template <int N>
     static __device__ __forceinline__ void stv(float* p, const float (&o)[N]) {
         if constexpr (N == 4) *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+        else if constexpr (N == 1) *p = o[0];
         else *reinterpret_cast<float2*>(p) = make_float2(o[0], o[1]);
     }
     static __device__ __forceinline__ float ld1(const float* p) { return __ldg(p); }
@@ -72,6 +75,8 @@ template <typename H, typename H2> struct IoHalf {
             const uint2 r = *reinterpret_cast<const uint2*>(p);
             const float2 a = C::to2(r.x), b = C::to2(r.y);
             o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+        } else if constexpr (N == 1) {
+            o[0] = C::to2((unsigned)*reinterpret_cast<const unsigned short*>(p)).x;
         } else {
             const unsigned r = *reinterpret_cast<const unsigned*>(p);
             const float2 a = C::to2(r);
@@ -85,6 +90,8 @@ template <typename H, typename H2> struct IoHalf {
             r.x = C::from2(o[0], o[1]);
             r.y = C::from2(o[2], o[3]);
             *reinterpret_cast<uint2*>(p) = r;
+        } else if constexpr (N == 1) {
+            *reinterpret_cast<unsigned short*>(p) = (unsigned short)(C::from2(o[0], 0.0f) & 0xffffu);
         } else {
             *reinterpret_cast<unsigned*>(p) = C::from2(o[0], o[1]);
         }

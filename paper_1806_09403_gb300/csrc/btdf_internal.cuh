@@ -132,13 +132,13 @@ struct BatchLbm {
 };
 
 // Launchers implemented in btdf_kernels.cu.
-// npl: nodes per lane (4 or 2; -4 / -2: software-pipelined kernel, pull
-// steps only); grid: upper bound on the blocks of the
-// persistent LBM kernel; pdl: launch as a programmatic dependent of the
-// preceding IB kernel (its non-band work overlaps the IB stage).
-cudaError_t launch_collide_stream(int storage, bool pull, int npl, const void* gin, void* gout,
+// variant: one of the register variants below (the software-pipelined ones
+// fall back to their plain form for an in-place step); grid: upper bound on
+// the blocks; pdl: launch as a programmatic dependent of the preceding IB
+// kernel (its non-band work overlaps the IB stage).
+cudaError_t launch_collide_stream(int storage, bool pull, int variant, const void* gin, void* gout,
                                   const LatticeParams& p, int grid, bool pdl, cudaStream_t st);
-int collide_stream_blocks_per_sm(int storage, bool pull, int npl);
+int collide_stream_blocks_per_sm(int storage, bool pull, int variant);
 
 // Kernel variants of the LBM step (btdf_tune): register-pipelined warps with
 // 4 or 2 nodes per lane, or TMA-tiled CTAs (tile rows x pipeline stages).
@@ -151,7 +151,9 @@ enum : int {
     kVarTma16x2 = 5,
     kVarReg4Pf = 6,
     kVarReg2Pf = 7,
-    kVarCount = 8
+    kVarReg1 = 8,      // 1 node per lane, 6 blocks per SM (<= 40 registers)
+    kVarReg2Occ = 9,   // 2 nodes per lane, 5 blocks per SM (<= 48 registers)
+    kVarCount = 10
 };
 // map: 3-D tensor map (x, y, population) of the input buffer with box
 // (128 + 2 * tma_halo(storage), tma_box_rows(variant), 9).

@@ -298,8 +298,10 @@ __device__ __forceinline__ void lbm_segment(const T* __restrict__ gin, T* __rest
     collide_store<T, NPL>(f, gout, p, y, xw, x0, live, seg);
 }
 
-// Persistent grid: each warp walks the row segments with a grid stride,
-// stepping its (row, segment) pair without integer division.
+// Each warp walks the row segments with a grid stride, stepping its (row,
+// segment) pair without integer division.  The host normally launches one
+// segment per warp, so the block scheduler balances the SMs; a capped grid
+// makes the kernel persistent.
 template <typename T, bool kPull, int NPL, int MINB>
 __global__ void __launch_bounds__(kThreads, MINB)
 collide_stream_kernel(const T* __restrict__ gin, T* __restrict__ gout, LatticeParams p) {
@@ -874,11 +876,7 @@ inline unsigned blocks_for(long long threads) {
     return (unsigned)((threads + kThreads - 1) / kThreads);
 }
 
-template <int NPL> struct Variant;
-template <> struct Variant<4> { static constexpr int MINB = 3; };   // <= 80 registers
-template <> struct Variant<2> { static constexpr int MINB = 4; };   // <= 64 registers
-
-template <typename T, int NPL>
+template <typename T, int NPL, int MB>
 cudaError_t collide_stream_tn(bool pull, const void* gin, void* gout, LatticeParams p, int grid,
                               bool pdl, cudaStream_t st) {
     constexpr int SW = 32 * NPL;
@@ -896,7 +894,6 @@ cudaError_t collide_stream_tn(bool pull, const void* gin, void* gout, LatticePar
     cfg.numAttrs = pdl ? 1 : 0;
     const T* a = (const T*)gin;
     T* b = (T*)gout;
-    constexpr int MB = Variant<NPL>::MINB;
     if (pull) return cudaLaunchKernelEx(&cfg, collide_stream_kernel<T, true, NPL, MB>, a, b, p);
     return cudaLaunchKernelEx(&cfg, collide_stream_kernel<T, false, NPL, MB>, a, b, p);
 }
@@ -926,20 +923,29 @@ int pf_blocks_tn() {
     return n;
 }
 
+// Register variants: nodes per lane and the resident blocks per SM the
+// register budget is cut for (3 x 256 threads <= 80 registers, 4 <= 64,
+// 5 <= 48, 6 <= 40).
 template <typename T>
-cudaError_t collide_stream_t(bool pull, int npl, const void* gin, void* gout, const LatticeParams& p,
+cudaError_t collide_stream_t(bool pull, int variant, const void* gin, void* gout, const LatticeParams& p,
                              int grid, bool pdl, cudaStream_t st) {
-    if (pull && npl == -2) return collide_stream_pf_tn<T, 2>(gin, gout, p, grid, pdl, st);
-    if (pull && npl == -4) return collide_stream_pf_tn<T, 4>(gin, gout, p, grid, pdl, st);
-    if (npl < 0) npl = -npl;
-    if (npl == 2) return collide_stream_tn<T, 2>(pull, gin, gout, p, grid, pdl, st);
-    return collide_stream_tn<T, 4>(pull, gin, gout, p, grid, pdl, st);
+    switch (variant) {
+    case kVarReg4Pf:
+        if (pull) return collide_stream_pf_tn<T, 4>(gin, gout, p, grid, pdl, st);
+        return collide_stream_tn<T, 4, 3>(pull, gin, gout, p, grid, pdl, st);
+    case kVarReg2Pf:
+        if (pull) return collide_stream_pf_tn<T, 2>(gin, gout, p, grid, pdl, st);
+        return collide_stream_tn<T, 2, 4>(pull, gin, gout, p, grid, pdl, st);
+    case kVarReg2: return collide_stream_tn<T, 2, 4>(pull, gin, gout, p, grid, pdl, st);
+    case kVarReg1: return collide_stream_tn<T, 1, 6>(pull, gin, gout, p, grid, pdl, st);
+    case kVarReg2Occ: return collide_stream_tn<T, 2, 5>(pull, gin, gout, p, grid, pdl, st);
+    default: return collide_stream_tn<T, 4, 3>(pull, gin, gout, p, grid, pdl, st);
+    }
 }
 
-template <typename T, int NPL>
+template <typename T, int NPL, int MB>
 int blocks_per_sm_tn(bool pull) {
     int n = 0;
-    constexpr int MB = Variant<NPL>::MINB;
     if (pull)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, collide_stream_kernel<T, true, NPL, MB>,
                                                       kThreads, 0);
@@ -950,11 +956,15 @@ int blocks_per_sm_tn(bool pull) {
 }
 
 template <typename T>
-int blocks_per_sm_t(bool pull, int npl) {
-    if (pull && npl == -2) return pf_blocks_tn<T, 2>();
-    if (pull && npl == -4) return pf_blocks_tn<T, 4>();
-    if (npl < 0) npl = -npl;
-    return npl == 2 ? blocks_per_sm_tn<T, 2>(pull) : blocks_per_sm_tn<T, 4>(pull);
+int blocks_per_sm_t(bool pull, int variant) {
+    switch (variant) {
+    case kVarReg4Pf: return pull ? pf_blocks_tn<T, 4>() : blocks_per_sm_tn<T, 4, 3>(pull);
+    case kVarReg2Pf: return pull ? pf_blocks_tn<T, 2>() : blocks_per_sm_tn<T, 2, 4>(pull);
+    case kVarReg2: return blocks_per_sm_tn<T, 2, 4>(pull);
+    case kVarReg1: return blocks_per_sm_tn<T, 1, 6>(pull);
+    case kVarReg2Occ: return blocks_per_sm_tn<T, 2, 5>(pull);
+    default: return blocks_per_sm_tn<T, 4, 3>(pull);
+    }
 }
 
 template <typename T, int TH, int S>
@@ -1045,7 +1055,7 @@ cudaError_t batch_lbm_tn(bool pull, const void* gin, void* gout, const BatchLbm&
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
-    constexpr int MB = Variant<NPL>::MINB;
+    constexpr int MB = NPL == 4 ? 3 : 4;
     if (pull)
         return cudaLaunchKernelEx(&cfg, collide_stream_batch_kernel<T, true, NPL, MB>, (const T*)gin,
                                   (T*)gout, b);
@@ -1056,7 +1066,7 @@ cudaError_t batch_lbm_tn(bool pull, const void* gin, void* gout, const BatchLbm&
 template <typename T, int NPL>
 int batch_blocks_tn() {
     int n = 0, m = 0;
-    constexpr int MB = Variant<NPL>::MINB;
+    constexpr int MB = NPL == 4 ? 3 : 4;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, collide_stream_batch_kernel<T, true, NPL, MB>,
                                                   kThreads, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, collide_stream_batch_kernel<T, false, NPL, MB>,
@@ -1124,12 +1134,12 @@ cudaError_t launch_ib_force_batch(int storage, bool pull, int width, const void*
 }
 
 
-cudaError_t launch_collide_stream(int storage, bool pull, int npl, const void* gin, void* gout,
+cudaError_t launch_collide_stream(int storage, bool pull, int variant, const void* gin, void* gout,
                                   const LatticeParams& p, int grid, bool pdl, cudaStream_t st) {
     switch (storage) {
-    case kStoreF32: return collide_stream_t<float>(pull, npl, gin, gout, p, grid, pdl, st);
-    case kStoreF16: return collide_stream_t<__half>(pull, npl, gin, gout, p, grid, pdl, st);
-    case kStoreBF16: return collide_stream_t<__nv_bfloat16>(pull, npl, gin, gout, p, grid, pdl, st);
+    case kStoreF32: return collide_stream_t<float>(pull, variant, gin, gout, p, grid, pdl, st);
+    case kStoreF16: return collide_stream_t<__half>(pull, variant, gin, gout, p, grid, pdl, st);
+    case kStoreBF16: return collide_stream_t<__nv_bfloat16>(pull, variant, gin, gout, p, grid, pdl, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -1156,11 +1166,11 @@ int collide_stream_tma_blocks_per_sm(int storage, int variant) {
 int tma_box_rows(int variant) { return variant == kVarTma16x2 ? 18 : 10; }
 int tma_halo(int storage) { return storage == kStoreF32 ? 4 : 8; }
 
-int collide_stream_blocks_per_sm(int storage, bool pull, int npl) {
+int collide_stream_blocks_per_sm(int storage, bool pull, int variant) {
     switch (storage) {
-    case kStoreF16: return blocks_per_sm_t<__half>(pull, npl);
-    case kStoreBF16: return blocks_per_sm_t<__nv_bfloat16>(pull, npl);
-    default: return blocks_per_sm_t<float>(pull, npl);
+    case kStoreF16: return blocks_per_sm_t<__half>(pull, variant);
+    case kStoreBF16: return blocks_per_sm_t<__nv_bfloat16>(pull, variant);
+    default: return blocks_per_sm_t<float>(pull, variant);
     }
 }
 

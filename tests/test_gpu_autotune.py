@@ -32,7 +32,7 @@ def test_autotune_leaves_the_run_unchanged(first):
     b.step(first)
     mk = a.markers(0)
     chosen, ms = a.autotune(steps=3, flush_l2=(first == 0))
-    assert 1 <= chosen <= 7 and chosen in ms and all(t > 0 for t in ms.values())
+    assert 1 <= chosen < B.VARIANT_COUNT and chosen in ms and all(t > 0 for t in ms.values())
     assert ms[chosen] == min(ms.values())
     assert a.steps == first
     if first:
@@ -53,7 +53,7 @@ def test_batch_autotune_leaves_the_run_unchanged():
     a.step(20)
     b.step(20)
     chosen, ms = a.autotune(steps=3)
-    assert chosen in (1, 2) and all(t > 0 for t in ms.values())
+    assert chosen in (1, 2, 3, 4) and all(t > 0 for t in ms.values())
     a.step(80)
     b.step(80)
     for i in range(2):

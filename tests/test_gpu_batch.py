@@ -48,7 +48,7 @@ def mixed_cases():
     return cases
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
 def test_batch_matches_single_contexts_bitwise(variant):
     cases = mixed_cases()
     bt = B.Batch.from_cases(cases, history_len=300)

@@ -263,8 +263,8 @@ def test_graph_replay_matches_direct_launches():
     assert np.array_equal(a.forces(0)[0], b.forces(0)[0])
 
 
-VARIANTS = [(1, 0), (2, 0), (3, 0), (4, 0), (5, 0), (6, 0), (7, 0), (1, 7), (2, 1), (3, 5),
-            (5, 1), (6, 3), (7, 1)]
+VARIANTS = [(1, 0), (2, 0), (3, 0), (4, 0), (5, 0), (6, 0), (7, 0), (8, 0), (9, 0), (1, 7), (2, 1),
+            (3, 5), (5, 1), (6, 3), (7, 1), (8, 5), (9, 2)]
 
 
 @pytest.mark.parametrize("storage", [B.BTDF_F32, B.BTDF_F16DEV, B.BTDF_BF16DEV])
@@ -286,7 +286,7 @@ def test_kernel_variants_agree_bitwise(storage):
         for a, b in zip(outs[0], o):
             assert np.array_equal(a, b)
     with pytest.raises(B.BtdfError):
-        lat.tune(8, 0)
+        lat.tune(B.VARIANT_COUNT, 0)
 
 
 @pytest.mark.parametrize("variant", [1, 3, 5, 6, 7])
@@ -356,3 +356,27 @@ def test_device_pointer_readback():
     t = torch.zeros((case.ny, case.nx), dtype=torch.float32, device="cuda")
     lat.field_to_device(B.FIELD_UX, t.data_ptr())
     assert np.array_equal(t.cpu().numpy(), lat.field(B.FIELD_UX))
+
+
+def test_async_force_readback_and_staged_velocities():
+    """btdf_read_forces_async into page-locked memory gives what the
+    synchronous read gives; marker velocities set every step through the
+    staging ring reach the device in order (the run equals one with the
+    velocities set synchronously, step by step)."""
+    case = W.small_cylinder(delta=3)
+    a = B.Lattice.from_case(case, history_len=64)
+    b = B.Lattice.from_case(case, history_len=64)
+    n = len(case.bodies[0].X)
+    out = torch.zeros((40, 2), dtype=torch.float64).pin_memory()
+    for i in range(40):
+        ub = np.full(n, 1e-3 * (i % 7))
+        a.set_marker_velocity(0, ub, -ub)
+        a.step(1)
+        a.forces_async(0, a.steps - 1, 1, out.data_ptr() + 16 * i)
+        b.set_marker_velocity(0, ub, -ub)
+        b.step(1)
+        b.sync()
+    a.sync()
+    fx, fy = b.forces(0, 0, 40)
+    assert np.array_equal(out[:, 0].numpy(), fx) and np.array_equal(out[:, 1].numpy(), fy)
+    assert np.array_equal(a.field(B.FIELD_UX), b.field(B.FIELD_UX))
