@@ -91,7 +91,9 @@ typedef enum {
     BTDF_FIELD_RHO = 0,   /* density, Eq. 9 (ny*nx floats) */
     BTDF_FIELD_UX = 1,    /* unforced velocity u*, Eq. 10 (ny*nx floats) */
     BTDF_FIELD_UY = 2,
-    BTDF_FIELD_POPS = 3   /* populations f (not deviations), [9][ny][nx] floats */
+    BTDF_FIELD_POPS = 3,  /* populations f (not deviations), [9][ny][nx] floats */
+    BTDF_FIELD_FX = 4,    /* immersed-boundary force density of the last step, Eq. 15 */
+    BTDF_FIELD_FY = 5     /* (without the uniform body force gx, gy), ny*nx floats */
 } btdf_field;
 
 typedef struct {
@@ -135,6 +137,14 @@ int btdf_init_fields(btdf_ctx *ctx, const double *rho, const double *ux, const d
 int btdf_add_markers(btdf_ctx *ctx, int32_t n, const double *X, const double *Y,
                      const double *Ubx, const double *Uby, double ds, double drs,
                      int32_t *body_id);
+
+/* Adds a circular body: n markers equally spaced on the circle of diameter D
+ * about (cx, cy), X_l = cx + (D/2) cos(2 pi l / n), Y_l = cy + (D/2) sin(2 pi l / n),
+ * at rest, with arc length ds = pi D / n per marker and thickness drs (<= 0:
+ * the value of Sec. 4.4, as btdf_add_markers).  Errors: EINVAL (n < 1,
+ * D <= 0, support outside the lattice). */
+int btdf_add_cylinder(btdf_ctx *ctx, double cx, double cy, double D, int32_t n, double drs,
+                      int32_t *body_id);
 
 /* Replaces the prescribed marker velocities U_b of one body (host arrays of
  * that body's marker count, read before the call returns).  The upload is

@@ -22,7 +22,7 @@ BTDF_OK, BTDF_EINVAL, BTDF_ENOMEM, BTDF_ECUDA, BTDF_EUNSTABLE, BTDF_ETIMEOUT, BT
 BTDF_F32, BTDF_F16DEV, BTDF_BF16DEV = 0, 1, 2
 BTDF_BCX_PERIODIC, BTDF_BCX_INOUT = 0, 1
 BTDF_BCY_PERIODIC, BTDF_BCY_FREESLIP, BTDF_BCY_NOSLIP = 0, 1, 2
-FIELD_RHO, FIELD_UX, FIELD_UY, FIELD_POPS = 0, 1, 2, 3
+FIELD_RHO, FIELD_UX, FIELD_UY, FIELD_POPS, FIELD_FX, FIELD_FY = 0, 1, 2, 3, 4, 5
 LAYOUT_PLANES, LAYOUT_ROWS = 0, 1
 
 # Every symbol include/btdf.h declares.
@@ -38,7 +38,7 @@ EXPORTS = [
     "btdf_batch_sync", "btdf_batch_step_count", "btdf_batch_read_forces", "btdf_batch_read_field",
     "btdf_batch_last_error", "btdf_set_inflow", "btdf_move_markers", "btdf_adjoint_forward",
     "btdf_adjoint_backward", "btdf_adjoint_release", "btdf_autotune", "btdf_batch_autotune",
-    "btdf_read_forces_async",
+    "btdf_read_forces_async", "btdf_add_cylinder",
 ]
 STATIC_MAX_MARKERS = 2048
 VARIANT_COUNT = 10          # collide-stream variants 0 (automatic) .. 9, see btdf_tune
@@ -93,6 +93,8 @@ def lib() -> C.CDLL:
     L.btdf_read_forces.argtypes = [ctxp, C.c_int32, C.c_int64, C.c_int64, vp, vp]
     L.btdf_read_markers.argtypes = [ctxp, C.c_int32, vp, vp, vp, vp]
     L.btdf_read_forces_async.argtypes = [ctxp, C.c_int32, C.c_int64, C.c_int64, vp]
+    L.btdf_add_cylinder.argtypes = [ctxp, C.c_double, C.c_double, C.c_double, C.c_int32, C.c_double,
+                                    C.POINTER(C.c_int32)]
     L.btdf_read_field.argtypes = [ctxp, C.c_int32, vp, C.c_int32]
     L.btdf_step_count.argtypes = [ctxp]
     L.btdf_step_count.restype = C.c_int64
@@ -246,6 +248,13 @@ class Lattice:
                                     float(ds), float(drs or 0.0), C.byref(bid))
         self._check(rc, "btdf_add_markers")
         self.body_markers.append(n)
+        return bid.value
+
+    def add_cylinder(self, cx, cy, D, n, drs=0.0) -> int:
+        bid = C.c_int32(-1)
+        self._check(lib().btdf_add_cylinder(self._ctx, float(cx), float(cy), float(D), int(n),
+                                            float(drs or 0.0), C.byref(bid)), "btdf_add_cylinder")
+        self.body_markers.append(int(n))
         return bid.value
 
     def set_marker_velocity(self, body, Ubx, Uby):

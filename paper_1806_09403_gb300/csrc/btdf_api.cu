@@ -39,6 +39,33 @@ cudaError_t launch_l2_flush(void* buf, size_t bytes, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Immersed-boundary force density of the step whose Lagrangian forces
+// p.F holds (Eq. 15): the same node-centric gather the LBM kernel applies.
+__global__ void force_field_kernel(LatticeParams p, int comp, float* __restrict__ dst) {
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= (long long)p.nx * p.ny) return;
+    const int y = (int)(n / p.nx), x = (int)(n - (long long)y * p.nx);
+    float f = 0.0f;
+    if (p.seg_index != nullptr) {
+        const int seg = p.seg_index[y * p.nseg + x / kSeg];
+        if (seg >= 0) {
+            const int* ptr = p.seg_ptr + (long long)seg * (kSeg + 1) + (x % kSeg);
+            for (int k = ptr[0]; k < ptr[1]; k++) {
+                const CsrEntry c = p.csr[k];
+                const float2 F = p.F[c.marker];
+                f = __fmaf_rn(c.w, comp == 0 ? F.x : F.y, f);
+            }
+        }
+    }
+    dst[n] = f;
+}
+
+cudaError_t launch_force_field(const LatticeParams& p, int comp, float* dst, cudaStream_t st) {
+    const long long nn = (long long)p.nx * p.ny;
+    force_field_kernel<<<(unsigned)((nn + kThreads - 1) / kThreads), kThreads, 0, st>>>(p, comp, dst);
+    return cudaGetLastError();
+}
+
 size_t l2_flush_bytes() {
     int dev = 0, l2 = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess)
@@ -829,6 +856,20 @@ int btdf_add_markers(btdf_ctx* ctx, int32_t n, const double* X, const double* Y,
     return BTDF_OK;
 }
 
+int btdf_add_cylinder(btdf_ctx* ctx, double cx, double cy, double D, int32_t n, double drs,
+                      int32_t* body_id) {
+    if (!ctx) return BTDF_EINVAL;
+    if (n < 1 || !(D > 0.0) || !std::isfinite(D) || !std::isfinite(cx) || !std::isfinite(cy))
+        return fail(ctx, BTDF_EINVAL, "need n >= 1, D > 0 and a finite centre");
+    std::vector<double> X(n), Y(n);
+    for (int l = 0; l < n; l++) {
+        const double th = 2.0 * M_PI * (double)l / (double)n;
+        X[l] = cx + 0.5 * D * std::cos(th);
+        Y[l] = cy + 0.5 * D * std::sin(th);
+    }
+    return btdf_add_markers(ctx, n, X.data(), Y.data(), nullptr, nullptr, M_PI * D / (double)n, drs, body_id);
+}
+
 int btdf_set_marker_velocity(btdf_ctx* ctx, int32_t body, const double* Ubx, const double* Uby) {
     if (!ctx) return BTDF_EINVAL;
     if (body < 0 || body >= (int)ctx->bodies.size() || !Ubx || !Uby)
@@ -971,7 +1012,7 @@ int btdf_read_markers(btdf_ctx* ctx, int32_t body, float* Usx, float* Usy, float
 
 int btdf_read_field(btdf_ctx* ctx, int32_t kind, float* dst, int32_t dst_is_device) {
     if (!ctx) return BTDF_EINVAL;
-    if (kind < 0 || kind > 3 || !dst) return fail(ctx, BTDF_EINVAL, "bad field kind or null output");
+    if (kind < 0 || kind > 5 || !dst) return fail(ctx, BTDF_EINVAL, "bad field kind or null output");
     if (!ctx->has_fields) return fail(ctx, BTDF_ESTATE, "no fields");
     const size_t nn = (size_t)ctx->cfg.nx * ctx->cfg.ny * (kind == 3 ? 9 : 1);
     float* d = dst;
@@ -979,8 +1020,10 @@ int btdf_read_field(btdf_ctx* ctx, int32_t kind, float* dst, int32_t dst_is_devi
     int rc = BTDF_OK;
     auto run = [&]() -> int {
         const LatticeParams p = lattice_params(ctx);
-        CK(launch_read_field(ctx->cfg.storage, !ctx->poststream, ctx->g[ctx->cur], p, kind, d,
-                             ctx->stream));
+        if (kind >= 4) CK(launch_force_field(p, kind - 4, d, ctx->stream));
+        else
+            CK(launch_read_field(ctx->cfg.storage, !ctx->poststream, ctx->g[ctx->cur], p, kind, d,
+                                 ctx->stream));
         if (!dst_is_device)
             CK(cudaMemcpyAsync(dst, d, sizeof(float) * nn, cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));

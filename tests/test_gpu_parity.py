@@ -380,3 +380,35 @@ def test_async_force_readback_and_staged_velocities():
     fx, fy = b.forces(0, 0, 40)
     assert np.array_equal(out[:, 0].numpy(), fx) and np.array_equal(out[:, 1].numpy(), fy)
     assert np.array_equal(a.field(B.FIELD_UX), b.field(B.FIELD_UX))
+
+
+def test_force_field_readback_against_oracle():
+    """BTDF_FIELD_FX/FY: the immersed-boundary force density of the last step
+    (Eq. 15) against the oracle's, and its sum against the body force of the
+    same step (Eq. 27: sum_e f_e = sum_l F_l ds drs = -F_p)."""
+    case = W.small_cylinder(delta=3)
+    lat = B.Lattice.from_case(case, history_len=256)
+    sim = O.Sim.from_case(case)
+    lat.step(200)
+    sim.step(200)
+    gx, gy = lat.field(B.FIELD_FX), lat.field(B.FIELD_FY)
+    rx, ry = sim.force_field()
+    scale = max(np.abs(rx).max(), np.abs(ry).max())
+    assert np.abs(gx - rx).max() <= 1e-4 * scale and np.abs(gy - ry).max() <= 1e-4 * scale
+    assert np.count_nonzero(gx) > 0 and np.all(gx[:, 100:] == 0)     # band nodes only
+    fx, fy = lat.forces(0, 199, 1)
+    assert abs(gx.astype(np.float64).sum() + fx[0]) <= 1e-5 * abs(fx[0])
+    assert abs(gy.astype(np.float64).sum() + fy[0]) <= 1e-5 * max(abs(fy[0]), 1e-3 * abs(fx[0]))
+
+
+def test_add_cylinder_places_circle_markers():
+    case = W.small_cylinder(delta=3)
+    a = B.Lattice.from_case(case)
+    b = B.Lattice(case.nx, case.ny, case.tau, case.u_in, case.delta, case.nf, B.BTDF_F32,
+                  case.bc_x, case.bc_y)
+    b.init_fields(*case.initial_fields())
+    assert b.add_cylinder(40.0, 40.0, case.D, len(case.bodies[0].X)) == 0
+    a.step(100)
+    b.step(100)
+    np.testing.assert_allclose(b.field(B.FIELD_UX), a.field(B.FIELD_UX), rtol=0, atol=1e-7)
+    np.testing.assert_allclose(b.forces(0)[0], a.forces(0)[0], rtol=1e-5)
