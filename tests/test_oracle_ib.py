@@ -183,3 +183,15 @@ def test_mdf_iterations_reduce_slip():
     s1 = _slip(1.0, steps=200, nf=1)
     s4 = _slip(1.0, steps=200, nf=4)
     assert s4 < 0.6 * s1, (s1, s4)
+
+
+def test_btdf_single_pass_against_mdf_four_passes():
+    """Sec. 5.2 / Fig. 16 compare BTDF with one forcing pass against MDF
+    (drs = dh) with several.  On the 160 x 80 cylinder after 200 steps the
+    one-pass BTDF slip is no worse than four MDF passes (3.8e-3 against
+    3.9e-3 of U) and a third of one DF pass, at a quarter of MDF's IB work."""
+    btdf = _slip(O.drs_paper(3), steps=200, nf=1)
+    mdf4 = _slip(1.0, steps=200, nf=4)
+    df = _slip(1.0, steps=200, nf=1)
+    assert btdf <= mdf4, (btdf, mdf4)
+    assert btdf < 0.35 * df, (btdf, df)
