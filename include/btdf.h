@@ -75,8 +75,15 @@ typedef enum {
 } btdf_storage;
 
 /* x boundaries: periodic, or inlet at x = 0 (non-equilibrium extrapolation to
- * velocity (u_in, 0)) with a zero-gradient outlet at x = nx-1. */
-typedef enum { BTDF_BCX_PERIODIC = 0, BTDF_BCX_INOUT = 1 } btdf_bc_x;
+ * velocity (u_in, 0)) with a zero-gradient or convective outlet at x = nx-1
+ * (Sec. 5.2 names a convective outlet). */
+typedef enum {
+    BTDF_BCX_PERIODIC = 0,
+    BTDF_BCX_INOUT = 1,      /* inlet + zero-gradient outlet (copy of column nx-2) */
+    BTDF_BCX_CONVECTIVE = 2  /* inlet + convective outlet: d f / dt + u_in d f / dx = 0,
+                                implicit upwind, f(nx-1, t+1) = (f(nx-1, t) + u_in f(nx-2, t+1)) / (1 + u_in);
+                                markers must keep off the outlet column; not for the batch */
+} btdf_bc_x;
 /* y boundaries: periodic, free-slip walls (half-way specular reflection) or
  * no-slip walls (half-way bounce-back); walls sit half a node outside rows
  * 0 and ny-1. */
@@ -204,9 +211,11 @@ int btdf_read_field(btdf_ctx *ctx, int32_t kind, float *dst, int32_t dst_is_devi
 int64_t btdf_step_count(const btdf_ctx *ctx);
 
 /* Checkpoint of the populations and the step counter (not the force
- * history).  btdf_state_size gives the byte count; save copies to a host
- * buffer of at least that size; load restores a checkpoint of a context with
- * the same nx, ny and storage.  Errors: EINVAL (size or shape mismatch). */
+ * history), plus the outlet column buffer under the convective outlet.
+ * btdf_state_size gives the byte count; save copies to a host buffer of at
+ * least that size; load restores a checkpoint of a context with the same nx,
+ * ny, storage, layout and x boundary.  Errors: EINVAL (size or shape
+ * mismatch). */
 int btdf_state_size(btdf_ctx *ctx, size_t *bytes);
 int btdf_save_state(btdf_ctx *ctx, void *dst, size_t cap, size_t *used);
 int btdf_load_state(btdf_ctx *ctx, const void *src, size_t len);

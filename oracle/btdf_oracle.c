@@ -27,7 +27,9 @@
  *     periodic axes wrap.
  *   - Boundaries of the cylinder channel (Sec. 5.2 gives only their physical
  *     meaning): inlet x = 0 by non-equilibrium extrapolation from column 1
- *     with u = (u_in, 0); outlet x = nx-1 copies column nx-2; free-slip walls
+ *     with u = (u_in, 0); outlet x = nx-1 copies column nx-2 (bc_x = 1) or
+ *     follows the convective condition d f / dt + U d f / dx = 0 with
+ *     U = u_in, implicit upwind in time and space (bc_x = 2); free-slip walls
  *     by half-way specular reflection; no-slip walls by half-way bounce-back.
  *
  * Parity pins (tests/test_oracle_*.py): delta identities, equilibrium and
@@ -62,6 +64,7 @@ typedef struct {
 
 struct ora_sim {
     int nx, ny, bcx, bcy, delta, nf;
+    double *outlet_old;      /* [ny][9] outlet column before the last streaming (bc_x = 2) */
     double tau, u_in, gx, gy;
     double *f, *fpost;          /* [ny][nx][9] */
     double *rho, *ux, *uy;      /* moments; ux, uy are u* (updated by passes) */
@@ -149,7 +152,8 @@ void oracle_guo(double tau, double ux, double uy, double fx, double fy, double *
 ora_sim *oracle_create(int nx, int ny, double tau, double u_in, int bc_x, int bc_y,
                        double gx, double gy, int delta, int nf)
 {
-    if (nx < 3 || ny < 3 || !(tau > 0.5) || oracle_support_width(delta) == 0 || nf < 1)
+    if (nx < 3 || ny < 3 || !(tau > 0.5) || oracle_support_width(delta) == 0 || nf < 1 ||
+        bc_x < 0 || bc_x > 2)
         return NULL;
     ora_sim *s = (ora_sim *)calloc(1, sizeof(ora_sim));
     size_t nn = (size_t)nx * ny;
@@ -158,6 +162,7 @@ ora_sim *oracle_create(int nx, int ny, double tau, double u_in, int bc_x, int bc
     s->delta = delta; s->nf = nf;
     s->f = (double *)calloc(nn * 9, sizeof(double));
     s->fpost = (double *)calloc(nn * 9, sizeof(double));
+    s->outlet_old = (double *)calloc((size_t)ny * 9, sizeof(double));
     s->rho = (double *)calloc(nn, sizeof(double));
     s->ux = (double *)calloc(nn, sizeof(double));
     s->uy = (double *)calloc(nn, sizeof(double));
@@ -180,7 +185,7 @@ void oracle_destroy(ora_sim *s)
     if (!s) return;
     for (int i = 0; i < s->nb; i++) free_body(&s->b[i]);
     free(s->b);
-    free(s->f); free(s->fpost); free(s->rho); free(s->ux); free(s->uy);
+    free(s->f); free(s->fpost); free(s->rho); free(s->ux); free(s->uy); free(s->outlet_old);
     free(s->fx); free(s->fy); free(s->dfx); free(s->dfy);
     free(s);
 }
@@ -465,7 +470,7 @@ static void inlet_column(ora_sim *s)
 
 void oracle_apply_inlet(ora_sim *s)
 {
-    if (s->bcx == 1) inlet_column(s);
+    if (s->bcx >= 1) inlet_column(s);
 }
 
 static void stream_and_bc(ora_sim *s)
@@ -473,6 +478,10 @@ static void stream_and_bc(ora_sim *s)
     const int nx = s->nx, ny = s->ny;
     const int px = s->bcx == 0, py = s->bcy == 0;
     double *fn = s->f;
+    /* the outlet column before this streaming (convective outlet) */
+    if (s->bcx == 2)
+        for (int y = 0; y < ny; y++)
+            for (int a = 0; a < 9; a++) s->outlet_old[y * 9 + a] = fn[((size_t)y * nx + nx - 1) * 9 + a];
     /* Every entry is overwritten below; NaN marks any that is not. */
     for (size_t q = 0; q < (size_t)nx * ny * 9; q++) fn[q] = NAN;
     /* Push streaming: f(x + e_a, t + 1) = f_post(x, t). */
@@ -509,6 +518,14 @@ static void stream_and_bc(ora_sim *s)
         inlet_column(s);
         for (int y = 0; y < ny; y++)          /* outlet: zero gradient */
             for (int a = 0; a < 9; a++) FN(nx - 1, y, a) = FN(nx - 2, y, a);
+    } else if (s->bcx == 2) {
+        inlet_column(s);
+        /* convective outlet, d f / dt + U d f / dx = 0 with U = u_in,
+         * implicit upwind: f(N, t+1) = (f(N, t) + U f(N-1, t+1)) / (1 + U) */
+        const double U = s->u_in;
+        for (int y = 0; y < ny; y++)
+            for (int a = 0; a < 9; a++)
+                FN(nx - 1, y, a) = (s->outlet_old[y * 9 + a] + U * FN(nx - 2, y, a)) / (1.0 + U);
     }
 #undef FP
 #undef FN

@@ -25,7 +25,9 @@ extern "C" {
 
 typedef struct ora_sim ora_sim;
 
-/* bc_x: 0 periodic, 1 inlet (x = 0, velocity u_in) / zero-gradient outlet.
+/* bc_x: 0 periodic, 1 inlet (x = 0, velocity u_in) / zero-gradient outlet,
+ * 2 the same inlet with a convective outlet (d f / dt + u_in d f / dx = 0,
+ * implicit upwind in time and space).
  * bc_y: 0 periodic, 1 free-slip walls, 2 no-slip walls (half-way bounce-back).
  * delta: 2, 3, 4 (Eqs. 37-39) or 5 (4-point cosine).  nf: forcing passes. */
 ora_sim *oracle_create(int nx, int ny, double tau, double u_in, int bc_x, int bc_y,

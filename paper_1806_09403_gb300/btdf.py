@@ -20,7 +20,7 @@ from . import _build
 BTDF_OK, BTDF_EINVAL, BTDF_ENOMEM, BTDF_ECUDA, BTDF_EUNSTABLE, BTDF_ETIMEOUT, BTDF_ESTATE = \
     0, -1, -2, -3, -4, -5, -6
 BTDF_F32, BTDF_F16DEV, BTDF_BF16DEV = 0, 1, 2
-BTDF_BCX_PERIODIC, BTDF_BCX_INOUT = 0, 1
+BTDF_BCX_PERIODIC, BTDF_BCX_INOUT, BTDF_BCX_CONVECTIVE = 0, 1, 2
 BTDF_BCY_PERIODIC, BTDF_BCY_FREESLIP, BTDF_BCY_NOSLIP = 0, 1, 2
 FIELD_RHO, FIELD_UX, FIELD_UY, FIELD_POPS, FIELD_FX, FIELD_FY = 0, 1, 2, 3, 4, 5
 LAYOUT_PLANES, LAYOUT_ROWS = 0, 1

@@ -166,6 +166,7 @@ struct btdf_ctx {
     double2* d_hist = nullptr;
     unsigned long long* d_step = nullptr;
     int* d_status = nullptr;
+    float* d_outlet = nullptr;         // [9][ny] previous outlet column (convective outlet)
     std::vector<MarkerAux> aux_host;
     // Pinned host staging, so per-step host <-> device copies are true DMA
     // transfers and a step's inputs and outputs need one synchronization.
@@ -296,8 +297,12 @@ LatticeParams lattice_params(const btdf_ctx* ctx) {
     p.nxp = ctx->nxp;
     p.nseg = ctx->nseg;
     p.plane = ctx->plane;
-    p.bcx = ctx->cfg.bc_x;
+    // the convective outlet is the in/out channel plus an outlet column buffer
+    p.bcx = ctx->cfg.bc_x == BTDF_BCX_CONVECTIVE ? kBcxInout : ctx->cfg.bc_x;
     p.bcy = ctx->cfg.bc_y;
+    p.outlet = ctx->d_outlet;
+    p.uc_old = (float)(1.0 / (1.0 + ctx->cfg.u_in));
+    p.uc_new = (float)(ctx->cfg.u_in / (1.0 + ctx->cfg.u_in));
     p.omega = (float)(1.0 / ctx->cfg.tau);
     p.guo = (float)(1.0 - 0.5 / ctx->cfg.tau);
     p.u_in = (float)ctx->cfg.u_in;
@@ -549,6 +554,9 @@ int rebuild_markers(btdf_ctx* ctx) {
     return BTDF_OK;
 }
 
+// Bytes of the convective outlet's column buffer (0 for other boundaries).
+size_t outlet_bytes(const btdf_ctx* ctx) { return ctx->d_outlet ? sizeof(float) * 9 * ctx->cfg.ny : 0; }
+
 // Marker positions must be finite and their support must touch the lattice.
 int check_positions(btdf_ctx* ctx, int n, const double* X, const double* Y) {
     const int nx = ctx->cfg.nx, ny = ctx->cfg.ny;
@@ -713,7 +721,7 @@ int btdf_create(const btdf_config* cfg, void* stream, btdf_ctx** out) {
     if (support_width(c.delta) == 0) return BTDF_EINVAL;
     if (c.nf < 1 || c.nf > 64) return BTDF_EINVAL;
     if (c.storage < 0 || c.storage > 2) return BTDF_EINVAL;
-    if (c.bc_x < 0 || c.bc_x > 1 || c.bc_y < 0 || c.bc_y > 2) return BTDF_EINVAL;
+    if (c.bc_x < 0 || c.bc_x > 2 || c.bc_y < 0 || c.bc_y > 2) return BTDF_EINVAL;
     if (c.history_len < 1) return BTDF_EINVAL;
     if (c.layout != BTDF_LAYOUT_PLANES && c.layout != BTDF_LAYOUT_ROWS) return BTDF_EINVAL;
     if (!std::isfinite(c.u_in) || std::fabs(c.u_in) >= 0.5) return BTDF_EINVAL;
@@ -760,7 +768,8 @@ int btdf_create(const btdf_config* cfg, void* stream, btdf_ctx** out) {
         if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return bail(BTDF_ECUDA);
     *ctx->status_pin = 0;
     if (dalloc(ctx, &ctx->d_step, sizeof(unsigned long long)) != cudaSuccess ||
-        dalloc(ctx, &ctx->d_status, sizeof(int)) != cudaSuccess)
+        dalloc(ctx, &ctx->d_status, sizeof(int)) != cudaSuccess ||
+        (c.bc_x == BTDF_BCX_CONVECTIVE && dalloc(ctx, &ctx->d_outlet, sizeof(float) * 9 * c.ny) != cudaSuccess))
         return bail(BTDF_ECUDA);
     if (cudaMemsetAsync(ctx->d_step, 0, sizeof(unsigned long long), ctx->stream) != cudaSuccess ||
         cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream) != cudaSuccess ||
@@ -780,6 +789,7 @@ int btdf_destroy(btdf_ctx* ctx) {
     dfree(ctx, ctx->g[1]);
     dfree(ctx, ctx->d_step);
     dfree(ctx, ctx->d_status);
+    dfree(ctx, ctx->d_outlet);
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
     for (cudaEvent_t e : ctx->aux_ev)
         if (e) cudaEventDestroy(e);
@@ -807,6 +817,7 @@ int btdf_init_fields(btdf_ctx* ctx, const double* rho, const double* ux, const d
         const size_t bytes = (size_t)9 * ctx->plane * ctx->elem;
         CK(cudaMemsetAsync(ctx->g[0], 0, bytes, st));
         CK(cudaMemsetAsync(ctx->g[1], 0, bytes, st));
+        if (ctx->d_outlet) CK(cudaMemsetAsync(ctx->d_outlet, 0, sizeof(float) * 9 * ctx->cfg.ny, st));
         const LatticeParams p = lattice_params(ctx);
         CK(launch_init_equilibrium(ctx->cfg.storage, ctx->g[0], p, d, d + nn, d + 2 * nn, st));
         CK(cudaMemsetAsync(ctx->d_step, 0, sizeof(unsigned long long), st));
@@ -836,6 +847,10 @@ int btdf_add_markers(btdf_ctx* ctx, int32_t n, const double* X, const double* Y,
             return fail(ctx, BTDF_EINVAL, "marker velocity not finite");
     const int rcp = check_positions(ctx, n, X, Y);
     if (rcp != BTDF_OK) return rcp;
+    if (ctx->cfg.bc_x == BTDF_BCX_CONVECTIVE)
+        for (int l = 0; l < n; l++)   // the outlet column's buffer changes while the IB stage runs
+            if ((int)std::floor(X[l] - 0.5 * ctx->width) + ctx->width > ctx->cfg.nx - 2)
+                return fail(ctx, BTDF_EINVAL, "a marker support reaches the convective outlet column");
     Body B;
     B.first = ctx->nmark;
     B.n = n;
@@ -1037,7 +1052,7 @@ int btdf_read_field(btdf_ctx* ctx, int32_t kind, float* dst, int32_t dst_is_devi
 
 int btdf_state_size(btdf_ctx* ctx, size_t* bytes) {
     if (!ctx || !bytes) return BTDF_EINVAL;
-    *bytes = sizeof(StateHeader) + (size_t)9 * ctx->plane * ctx->elem;
+    *bytes = sizeof(StateHeader) + (size_t)9 * ctx->plane * ctx->elem + outlet_bytes(ctx);
     return BTDF_OK;
 }
 
@@ -1050,8 +1065,10 @@ int btdf_save_state(btdf_ctx* ctx, void* dst, size_t cap, size_t* used) {
     StateHeader h{kStateMagic, ctx->cfg.nx, ctx->cfg.ny, ctx->nxp, ctx->cfg.storage,
                   ctx->poststream ? 1 : 0, ctx->cfg.layout, ctx->steps};
     std::memcpy(dst, &h, sizeof(h));
-    CK(cudaMemcpyAsync((char*)dst + sizeof(h), ctx->g[ctx->cur], need - sizeof(h),
+    const size_t ob = outlet_bytes(ctx);
+    CK(cudaMemcpyAsync((char*)dst + sizeof(h), ctx->g[ctx->cur], need - sizeof(h) - ob,
                        cudaMemcpyDeviceToHost, ctx->stream));
+    if (ob) CK(cudaMemcpyAsync((char*)dst + need - ob, ctx->d_outlet, ob, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     if (used) *used = need;
     return read_status(ctx);
@@ -1067,8 +1084,10 @@ int btdf_load_state(btdf_ctx* ctx, const void* src, size_t len) {
     if (h.magic != kStateMagic || h.nx != ctx->cfg.nx || h.ny != ctx->cfg.ny || h.nxp != ctx->nxp ||
         h.storage != ctx->cfg.storage || h.layout != ctx->cfg.layout || h.steps < 0)
         return fail(ctx, BTDF_EINVAL, "checkpoint does not match this context");
-    CK(cudaMemcpyAsync(ctx->g[ctx->cur], (const char*)src + sizeof(h), need - sizeof(h),
+    const size_t ob = outlet_bytes(ctx);
+    CK(cudaMemcpyAsync(ctx->g[ctx->cur], (const char*)src + sizeof(h), need - sizeof(h) - ob,
                        cudaMemcpyHostToDevice, ctx->stream));
+    if (ob) CK(cudaMemcpyAsync(ctx->d_outlet, (const char*)src + need - ob, ob, cudaMemcpyHostToDevice, ctx->stream));
     unsigned long long s = (unsigned long long)h.steps;
     CK(cudaMemcpyAsync(ctx->d_step, &s, sizeof(s), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -1150,6 +1169,8 @@ int btdf_adjoint_forward(btdf_ctx* ctx, int64_t nsteps, int32_t every, int32_t b
     if (ctx->nmark == 0) return fail(ctx, BTDF_ESTATE, "the objective needs at least one body");
     if (ctx->cfg.nf != 1 || ctx->cfg.storage != BTDF_F32)
         return fail(ctx, BTDF_EINVAL, "the adjoint supports nf = 1 with FP32 storage");
+    if (ctx->cfg.bc_x == BTDF_BCX_CONVECTIVE)
+        return fail(ctx, BTDF_EINVAL, "the adjoint supports the zero-gradient outlet only");
     if (nsteps < 1 || every < 1 || nsteps > (1ll << 30))
         return fail(ctx, BTDF_EINVAL, "need nsteps >= 1 and every >= 1");
     if (!(dref > 0.0) || !std::isfinite(dref)) return fail(ctx, BTDF_EINVAL, "need dref > 0");

@@ -212,7 +212,8 @@ __device__ void pull_raw(const T* __restrict__ g, const LatticeParams& p, int x,
 // Post-streaming deviations with every boundary rule: inlet column by
 // non-equilibrium extrapolation from column 1 to u = (u_in, 0),
 // f(0) = f(1) + f_eq(rho_1, u_in) - f_eq(rho_1, u*_1); outlet column copied
-// from column nx-2.
+// from column nx-2, or, with the convective outlet, relaxed towards it from
+// the previous step's outlet column.
 template <typename T>
 __device__ void pull_node(const T* __restrict__ g, const LatticeParams& p, int x, int y, float f[9]) {
     if (p.bcx == kBcxInout && x == 0) {
@@ -227,6 +228,12 @@ __device__ void pull_node(const T* __restrict__ g, const LatticeParams& p, int x
                                 eq_part_diff(a, p.urx, p.ury, m.dux, m.duy));
     } else if (p.bcx == kBcxInout && x == p.nx - 1) {
         pull_raw<T>(g, p, p.nx - 2, y, f);
+        if (p.outlet != nullptr) {
+            // convective outlet, implicit upwind: (old + U f(N-1)) / (1 + U)
+#pragma unroll
+            for (int a = 0; a < 9; a++)
+                f[a] = __fmaf_rn(p.uc_new, f[a], __fmul_rn(p.uc_old, p.outlet[a * p.ny + y]));
+        }
     } else {
         pull_raw<T>(g, p, x, y, f);
     }

@@ -87,6 +87,11 @@ struct LatticeParams {
     //   c1 = 3 + 9 e.U_r,  k = 1 + P_a(U_r),  wom = w_a / tau,  wg = w_a (1 - 1/(2 tau)).
     float eur[9], c1[9], kr[9], wom[9], wg[9];
     float gx, gy;              // uniform body force
+    // Convective outlet (null: zero-gradient): the outlet column's
+    // post-streaming deviations of the previous step, [9][ny], and the
+    // weights of f(N, t+1) = old / (1 + U) + U / (1 + U) f(N-1, t+1).
+    float* outlet;
+    float uc_old, uc_new;
     const int* seg_index;      // [ny * nseg] band segment id or -1 (null: no band)
     const int* seg_ptr;        // [nband * (kSeg + 1)] CSR row pointers per node
     const CsrEntry* csr;

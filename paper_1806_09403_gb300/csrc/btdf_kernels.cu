@@ -78,6 +78,19 @@ __device__ __forceinline__ void collide_store(float (&f)[9][NPL], T* __restrict_
                                               const LatticeParams& p, int y, int xw, int x0,
                                               bool live, int seg) {
     const unsigned rowoff = (unsigned)y * p.rs + (unsigned)x0;
+    // Convective outlet: keep this step's post-streaming outlet column for
+    // the next step's boundary rule.
+    if (p.outlet != nullptr && live && x0 + NPL > p.nx - 1 && x0 <= p.nx - 1) {
+        const int i = p.nx - 1 - x0;
+#pragma unroll
+        for (int a = 0; a < 9; a++) {
+            float v = f[a][0];
+#pragma unroll
+            for (int k = 1; k < NPL; k++)
+                if (k == i) v = f[a][k];
+            p.outlet[a * p.ny + y] = v;
+        }
+    }
     // Force density on this lane's nodes: node-centric spread (Eq. 15) of the
     // Lagrangian forces over band segments (after the IB kernel has finished),
     // plus the uniform body force.

@@ -1,0 +1,128 @@
+"""Parity at the full sizes of the benchmarked configurations, in the launch
+configuration bench.py times (default variant, one row segment per warp,
+CUDA-graph replay):
+
+* the 8192 x 4096 lattice with 400 cylinders (D = 20, 63 markers each),
+  FP32, against the FP64 oracle over 100 steps: velocity field and the drag
+  and lift of every one of the 400 bodies, spec bars;
+* the 512-lattice batch (lattices of 128 x 64 .. 1024 x 512): four sampled
+  lattices against the oracle over 200 steps;
+* the 800 x 400 adjoint window (500 steps after 2000, checkpoint every 50):
+  dJ/dU against central differences of the FP64 oracle (eps = 1e-4), which
+  starts from the oracle's own state after the same 2000 steps.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import oracle as O
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1806_09403_gb300 import _build  # noqa: E402
+from paper_1806_09403_gb300 import btdf as B  # noqa: E402
+from paper_1806_09403_gb300.autograd import DragWindow  # noqa: E402
+
+VEL_TOL = 1e-5
+CD_TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    _build.build()
+    O.set_threads(min(os.cpu_count() or 1, 64))
+
+
+def vel_err(lat, sim):
+    _, ux, uy = lat.moments()
+    _, rx, ry = sim.moments()
+    num = ((ux.astype(np.float64) - rx) ** 2 + (uy.astype(np.float64) - ry) ** 2).sum()
+    return float(np.sqrt(num / (rx ** 2 + ry ** 2).sum()))
+
+
+def force_err(gx, gy, rx, ry):
+    """Largest per-step Cd / Cl error on the drag scale (the bars of the
+    cylinder parity tests)."""
+    scale = np.abs(rx).mean()
+    ecd = np.abs(gx - rx) / np.maximum(np.abs(rx), scale)
+    ecl = np.abs(gy - ry) / np.maximum(np.maximum(np.abs(ry), np.abs(rx)), scale)
+    return float(ecd.max()), float(ecl.max())
+
+
+def test_many_cylinders_8192x4096_100_steps():
+    case = W.many_cylinders()
+    lat = B.Lattice.from_case(case, history_len=128)
+    sim = O.Sim.from_case(case)
+    lat.step(100)
+    sim.step(100)
+    e = vel_err(lat, sim)
+    worst = (0.0, 0.0)
+    for b in range(len(case.bodies)):
+        gx, gy = lat.forces(b, 0, 100)
+        rx, ry = sim.history(b, 0, 100)
+        ecd, ecl = force_err(gx, gy, rx, ry)
+        worst = (max(worst[0], ecd), max(worst[1], ecl))
+    print(f"\n[8192x4096, 400 cylinders, 100 steps] velocity rel L2 {e:.2e}, "
+          f"worst Cd {worst[0]:.2e}, worst Cl {worst[1]:.2e} over 400 bodies")
+    assert e <= VEL_TOL
+    assert worst[0] <= CD_TOL and worst[1] <= CD_TOL
+
+
+def test_batch_512_sampled_lattices():
+    cases = W.batch_cases(512, seed=7)
+    bt = B.Batch.from_cases(cases, history_len=256)
+    bt.step(200)
+    first_body = np.cumsum([0] + [len(c.bodies) for c in cases])
+    sample = [0, 137, 301, 511]
+    for i in sample:
+        c = cases[i]
+        sim = O.Sim.from_case(c)
+        sim.step(200)
+        _, rx, ry = sim.moments()
+        ux, uy = bt.field(i, B.FIELD_UX), bt.field(i, B.FIELD_UY)
+        e = float(np.sqrt((((ux - rx) ** 2 + (uy - ry) ** 2).sum()) / ((rx ** 2 + ry ** 2).sum())))
+        gx, gy = bt.forces(int(first_body[i]), 0, 200)
+        hx, hy = sim.history(0, 0, 200)
+        ecd, ecl = force_err(gx, gy, hx, hy)
+        print(f"\n[batch lattice {i}: {c.nx}x{c.ny}, Re {c.Re:g}] velocity {e:.2e}, Cd {ecd:.2e}, Cl {ecl:.2e}")
+        assert e <= max(VEL_TOL, 200 * 2.0 ** -24)
+        assert ecd <= CD_TOL and ecl <= CD_TOL
+
+
+def test_adjoint_800x400_inflow_gradient_against_fp64():
+    case = W.adjoint_cylinder()
+    t0, n, eps = 2000, 500, 1e-4
+    lat = B.Lattice.from_case(case, history_len=256)
+    lat.step(t0)
+    win = DragWindow.for_lattice(lat, 200.0, 200.0, 0.5 * case.D, n, every=50, dref=case.D)
+    z = np.zeros(len(case.bodies[0].X))
+    J = win.evaluate(case.u_in, z)
+    dU, _ = win.gradients(case.u_in, z)
+
+    base = O.Sim.from_case(case)
+    base.step(t0)
+    start = base.pops()
+    b = case.bodies[0]
+
+    def window(u):
+        s = O.Sim(case.nx, case.ny, case.tau, u, case.bc_x, case.bc_y, 0.0, 0.0, case.delta, case.nf)
+        s.init_fields(*case.initial_fields())
+        s.set_pops(start)
+        s.apply_inlet()
+        s.add_body(b.X, b.Y, b.ds, drs=case.drs)
+        s.step(n)
+        fx, _ = s.history(0)
+        return float(np.mean(fx) / (0.5 * u * u * case.D))
+
+    J64 = window(case.u_in)
+    fd = (window(case.u_in + eps) - window(case.u_in - eps)) / (2 * eps)
+    print(f"\n[800x400 adjoint] J {J:.8f} (FP64 {J64:.8f}); dJ/dU adjoint {dU:.6e}, FP64 FD {fd:.6e} "
+          f"({abs(dU / fd - 1):.1e})")
+    assert abs(J / J64 - 1) <= 1e-4
+    assert abs(dU / fd - 1) <= 1e-3

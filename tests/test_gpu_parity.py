@@ -412,3 +412,35 @@ def test_add_cylinder_places_circle_markers():
     b.step(100)
     np.testing.assert_allclose(b.field(B.FIELD_UX), a.field(B.FIELD_UX), rtol=0, atol=1e-7)
     np.testing.assert_allclose(b.forces(0)[0], a.forces(0)[0], rtol=1e-5)
+
+
+def test_convective_outlet_1000_steps():
+    """The 160 x 80 cylinder with the convective outlet (Sec. 5.2) against
+    the oracle over 1000 steps (spec bars), the outlet column buffer
+    carried through a checkpoint (bitwise), and the kernel variants agreeing
+    bitwise on it."""
+    case = W.small_cylinder(delta=4)
+    case.bc_x = W.BCX_CONVECTIVE
+    lat, sim = run_both(case, 1000, chunks=[1, 63, 64, 872])
+    check_fields(lat, sim)
+    check_forces(lat, sim, case)
+    a = B.Lattice.from_case(case, history_len=600)
+    a.step(300)
+    blob = a.save_state()
+    a.step(300)
+    b = B.Lattice.from_case(case, history_len=600)
+    b.load_state(blob)
+    b.step(300)
+    assert np.array_equal(a.field(B.FIELD_UX), b.field(B.FIELD_UX))
+    outs = []
+    for variant in (1, 2, 3, 9):
+        c = B.Lattice.from_case(case)
+        c.tune(variant, 0)
+        c.step(120)
+        outs.append(c.field(B.FIELD_POPS))
+    for o in outs[1:]:
+        assert np.array_equal(outs[0], o)
+    z = W.small_cylinder(delta=4)
+    zg = B.Lattice.from_case(z)
+    zg.step(120)
+    assert not np.array_equal(zg.field(B.FIELD_POPS)[:, :, -1], outs[0][:, :, -1])

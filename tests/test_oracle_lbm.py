@@ -100,6 +100,8 @@ def _uniform_case(bc_x, bc_y, u=(0.04, 0.0), steps=50):
     (W.BCX_PERIODIC, W.BCY_FREESLIP, (0.04, 0.0)),
     (W.BCX_INOUT, W.BCY_FREESLIP, (0.04, 0.0)),
     (W.BCX_INOUT, W.BCY_PERIODIC, (0.04, 0.0)),
+    (W.BCX_CONVECTIVE, W.BCY_FREESLIP, (0.04, 0.0)),
+    (W.BCX_CONVECTIVE, W.BCY_PERIODIC, (0.04, 0.0)),
     (W.BCX_PERIODIC, W.BCY_NOSLIP, (0.0, 0.0)),
 ])
 def test_uniform_flow_is_exact_steady_state(bcx, bcy, u):
@@ -176,6 +178,42 @@ def test_inlet_extrapolation_imposes_velocity():
     assert np.abs(r[:, 0] - r[:, 1]).max() < 1e-14
     f = s.pops()
     assert np.abs(f[:, -1, :] - f[:, -2, :]).max() == 0.0
+
+
+def test_convective_outlet_holds_its_column_without_inflow():
+    """With U = 0 the convective condition d f / dt + U d f / dx = 0 reads
+    d f / dt = 0: the outlet column keeps its initial populations exactly,
+    whatever the flow next to it does."""
+    nx, ny = 24, 10
+    rng = np.random.default_rng(3)
+    s = O.Sim(nx, ny, 0.7, 0.0, W.BCX_CONVECTIVE, W.BCY_FREESLIP, 0.0, 0.0, 3, 1)
+    s.init_fields(1.0 + 1e-3 * rng.standard_normal((ny, nx)), 0.02 * rng.standard_normal((ny, nx)),
+                  0.02 * rng.standard_normal((ny, nx)))
+    f0 = s.pops()
+    s.step(30)
+    f = s.pops()
+    assert np.array_equal(f[:, -1, :], f0[:, -1, :])
+    assert not np.array_equal(f[:, -2, :], f0[:, -2, :])
+
+
+def test_convective_outlet_relaxes_towards_its_neighbour():
+    """Each step moves the outlet column a fraction U / (1 + U) of the way
+    from its previous value to the new neighbouring column (implicit upwind),
+    so it always lies between the two; with U > 0 an outlet column that
+    starts away from the neighbour's state converges to it."""
+    c = W.small_cylinder(delta=3)
+    c.bc_x = W.BCX_CONVECTIVE
+    s = O.Sim.from_case(c)
+    s.step(50)
+    old = s.pops()[:, -1, :]
+    s.step(1)
+    f = s.pops()
+    lo = np.minimum(old, f[:, -2, :]) - 1e-15
+    hi = np.maximum(old, f[:, -2, :]) + 1e-15
+    assert np.all(f[:, -1, :] >= lo) and np.all(f[:, -1, :] <= hi)
+    z = O.Sim.from_case(W.small_cylinder(delta=3))
+    z.step(51)
+    assert not np.array_equal(f[:, -1, :], z.pops()[:, -1, :])   # not the zero-gradient copy
 
 
 def _poiseuille(tau, ny=16, g=1e-6, steps=None):

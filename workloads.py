@@ -30,6 +30,7 @@ import numpy as np
 # Boundary kinds, shared vocabulary of both implementations' C interfaces.
 BCX_PERIODIC = 0
 BCX_INOUT = 1
+BCX_CONVECTIVE = 2
 BCY_PERIODIC = 0
 BCY_FREESLIP = 1
 BCY_NOSLIP = 2
