@@ -97,6 +97,9 @@ struct LatticeParams {
     const CsrEntry* csr;
     const float2* F;           // Lagrangian forces of the step (sum of passes)
     unsigned long long* step;  // device step counter, advanced by the LBM kernel
+    // Register variants: prefetch into L2 the row segment this many units
+    // ahead (about half a wave of resident warps later; 0: off).
+    int pf_ahead;
     int* status;               // sticky device status bits
     // Force on each body (Eq. 27), reduced in FP64 by block 0 of the LBM kernel.
     int nbody;
@@ -158,7 +161,8 @@ enum : int {
     kVarReg2Pf = 7,
     kVarReg1 = 8,      // 1 node per lane, 6 blocks per SM (<= 40 registers)
     kVarReg2Occ = 9,   // 2 nodes per lane, 5 blocks per SM (<= 48 registers)
-    kVarCount = 10
+    kVarReg2OccPf = 10, // as 9, each warp also prefetches a later row segment into L2
+    kVarCount = 11
 };
 // map: 3-D tensor map (x, y, population) of the input buffer with box
 // (128 + 2 * tma_halo(storage), tma_box_rows(variant), 9).

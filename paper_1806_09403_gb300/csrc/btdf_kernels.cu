@@ -328,6 +328,23 @@ collide_stream_kernel(const T* __restrict__ gin, T* __restrict__ gout, LatticePa
     // Band segments wait for the IB kernel's forces inside lbm_segment; the
     // body-force reduction comes after block 0's lattice work, when the IB
     // kernel has long finished.
+    // L2 prefetch of the segment a later wave of warps will process: its
+    // loads then hit L2 instead of waiting on DRAM (one instruction per warp).
+    if (p.pf_ahead > 0) {
+        const long long u2 = (long long)w0 + p.pf_ahead;
+        if (u2 < (long long)p.ny * nsegw) {
+            const int y2 = (int)(u2 / nsegw), x2 = (int)(u2 - (long long)y2 * nsegw) * SW;
+            constexpr int LE = 128 / (int)sizeof(T);            // elements per 128-byte line
+            constexpr int LINES = (SW + LE - 1) / LE;
+            for (int k = lane; k < 9 * LINES; k += 32) {
+                const int a = k / LINES, xl = x2 + (k - a * LINES) * LE;
+                if (xl < p.nxp) {
+                    const T* addr = gin + p.poff[a] + (unsigned)y2 * p.rs + (unsigned)xl;
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(addr));
+                }
+            }
+        }
+    }
     int y = y0, s = s0;
     while (y < p.ny) {
         const int seg = band_segment(p, y, s * SW);
@@ -951,7 +968,8 @@ cudaError_t collide_stream_t(bool pull, int variant, const void* gin, void* gout
         return collide_stream_tn<T, 2, 4>(pull, gin, gout, p, grid, pdl, st);
     case kVarReg2: return collide_stream_tn<T, 2, 4>(pull, gin, gout, p, grid, pdl, st);
     case kVarReg1: return collide_stream_tn<T, 1, 6>(pull, gin, gout, p, grid, pdl, st);
-    case kVarReg2Occ: return collide_stream_tn<T, 2, 5>(pull, gin, gout, p, grid, pdl, st);
+    case kVarReg2Occ:
+    case kVarReg2OccPf: return collide_stream_tn<T, 2, 5>(pull, gin, gout, p, grid, pdl, st);
     default: return collide_stream_tn<T, 4, 3>(pull, gin, gout, p, grid, pdl, st);
     }
 }
@@ -975,7 +993,8 @@ int blocks_per_sm_t(bool pull, int variant) {
     case kVarReg2Pf: return pull ? pf_blocks_tn<T, 2>() : blocks_per_sm_tn<T, 2, 4>(pull);
     case kVarReg2: return blocks_per_sm_tn<T, 2, 4>(pull);
     case kVarReg1: return blocks_per_sm_tn<T, 1, 6>(pull);
-    case kVarReg2Occ: return blocks_per_sm_tn<T, 2, 5>(pull);
+    case kVarReg2Occ:
+    case kVarReg2OccPf: return blocks_per_sm_tn<T, 2, 5>(pull);
     default: return blocks_per_sm_tn<T, 4, 3>(pull);
     }
 }

@@ -56,6 +56,17 @@ def test_invalid_config_rejected_on_host(field, value):
     assert not ctx
 
 
+def test_lattice_beyond_32bit_offsets_rejected_on_host():
+    """Element offsets inside the kernels are 32-bit: 9 x nxp x ny must stay
+    below 2^32 (nxp = nx rounded up to 32).  32768 x 14563 is the largest
+    lattice of that width; one more row is refused before any device call."""
+    cfg = B.btdf_config_default()
+    cfg.nx, cfg.ny = 32768, 14564
+    assert 9 * 32768 * 14564 >= 2 ** 32 > 9 * 32768 * 14563
+    rc, ctx = B.btdf_create(cfg)
+    assert rc == B.BTDF_EINVAL and not ctx
+
+
 def test_null_arguments_rejected():
     L = B.lib()
     assert L.btdf_create(None, None, None) == B.BTDF_EINVAL

@@ -9,7 +9,9 @@ CUDA-graph replay):
   lattices against the oracle over 200 steps;
 * the 800 x 400 adjoint window (500 steps after 2000, checkpoint every 50):
   dJ/dU against central differences of the FP64 oracle (eps = 1e-4), which
-  starts from the oracle's own state after the same 2000 steps.
+  starts from the oracle's own state after the same 2000 steps;
+* the largest lattice the 32-bit element offsets allow, by translation
+  invariance against a small lattice.
 """
 import os
 
@@ -126,3 +128,44 @@ def test_adjoint_800x400_inflow_gradient_against_fp64():
           f"({abs(dU / fd - 1):.1e})")
     assert abs(J / J64 - 1) <= 1e-4
     assert abs(dU / fd - 1) <= 1e-3
+
+
+def test_largest_lattice_32bit_offsets():
+    """The largest lattice of width 32768 the 32-bit element offsets allow
+    (32768 x 14563: 9 x nxp x ny just below 2^32, 34 GB of FP32 populations),
+    fully periodic, uniform flow, one cylinder near the far corner where the
+    offsets are largest.  Translation invariance: after 20 steps the flow
+    around that cylinder equals the flow around the same cylinder (same
+    fractional position) in a 128 x 128 periodic lattice, and the lattice far
+    from it is still the uniform state."""
+    nx, ny, tau, u = 32768, 14563, 0.6, (0.03, 0.01)
+    d, n = 16.0, 50
+    cx, cy = nx - 60.3, ny - 60.7
+    big = B.Lattice(nx, ny, tau, 0.0, 3, 1, B.BTDF_F32, B.BTDF_BCX_PERIODIC, B.BTDF_BCY_PERIODIC,
+                    history_len=32)
+    big.init_fields(np.ones((ny, nx)), np.full((ny, nx), u[0]), np.full((ny, nx), u[1]))
+    big.add_cylinder(cx, cy, d, n)
+    ox, oy = nx - 128, ny - 128            # the small lattice is this window
+    small = B.Lattice(128, 128, tau, 0.0, 3, 1, B.BTDF_F32, B.BTDF_BCX_PERIODIC, B.BTDF_BCY_PERIODIC,
+                      history_len=32)
+    small.init_fields(np.ones((128, 128)), np.full((128, 128), u[0]), np.full((128, 128), u[1]))
+    small.add_cylinder(cx - ox, cy - oy, d, n)
+    big.step(20)
+    small.step(20)
+    dev = torch.empty((ny, nx), dtype=torch.float32, device="cuda")
+    for kind in (B.FIELD_UX, B.FIELD_UY, B.FIELD_RHO):
+        big.field_to_device(kind, dev.data_ptr())
+        torch.cuda.synchronize()
+        win = dev[oy:, ox:].cpu().numpy()
+        ref = small.field(kind)
+        # the cylinder and the 20-node front around it lie inside the window
+        inner = (slice(16, 128), slice(16, 128))
+        np.testing.assert_allclose(win[inner], ref[inner], rtol=0, atol=2e-7)
+        far = dev[: ny // 2, : nx // 2]
+        val = {B.FIELD_UX: u[0], B.FIELD_UY: u[1], B.FIELD_RHO: 1.0}[kind]
+        assert float((far - val).abs().max()) < 1e-6
+    del dev
+    fb, fs = big.forces(0), small.forces(0)
+    np.testing.assert_allclose(fb[0], fs[0], rtol=1e-5)
+    big.close()
+
