@@ -4,7 +4,7 @@ CUDA-graph replay):
 
 * the 8192 x 4096 lattice with 400 cylinders (D = 20, 63 markers each),
   FP32, against the FP64 oracle over 100 steps: velocity field and the drag
-  and lift of every one of the 400 bodies, north-star bars;
+  and lift of every one of the 400 bodies (velocity 1e-5, Cd and Cl 1e-4);
 * the 512-lattice batch (lattices of 128 x 64 .. 1024 x 512): four sampled
   lattices against the oracle over 200 steps;
 * the 800 x 400 adjoint window (500 steps after 2000, checkpoint every 50):

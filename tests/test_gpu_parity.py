@@ -416,7 +416,7 @@ def test_add_cylinder_places_circle_markers():
 
 def test_convective_outlet_1000_steps():
     """The 160 x 80 cylinder with the convective outlet (Sec. 5.2) against
-    the oracle over 1000 steps (spec bars), the outlet column buffer
+    the oracle over 1000 steps (velocity 1e-5, Cd and Cl 1e-4), the outlet column buffer
     carried through a checkpoint (bitwise), and the kernel variants agreeing
     bitwise on it."""
     case = W.small_cylinder(delta=4)
