@@ -295,7 +295,10 @@ int btdf_autotune(btdf_ctx *ctx, int32_t steps, int32_t flush_l2, int32_t *chose
  * interpolation at the band nodes).  Outputs (host, any may be NULL):
  * dJdU = dJ/du_in, dJdX[l], dJdY[l] = dJ/dX_l, dJ/dY_l for every marker in the
  * order the markers were added.  Setting the inflow, moving markers or
- * changing marker velocities invalidates the window (ESTATE).  Synchronizes. */
+ * changing marker velocities invalidates the window (ESTATE).  Synchronizes.
+ * Both passes are replayed as CUDA graphs captured on first use (on an
+ * internal stream) and updated in place when the window, the markers or the
+ * inflow change. */
 int btdf_adjoint_forward(btdf_ctx *ctx, int64_t nsteps, int32_t every, int32_t body, double dref,
                          double *J);
 int btdf_adjoint_backward(btdf_ctx *ctx, double *dJdU, double *dJdX, double *dJdY);

@@ -130,6 +130,11 @@ struct AdjointTape {
     float4* mbar = nullptr;
     double* acc = nullptr;       // [2 nmark + 1]: dJ/dX, dJ/dY, inlet part of dJ/dU
     size_t bytes = 0;
+    long long gen = 0;           // bumped whenever the buffers are reallocated
+    // The window's forward pass and its reverse sweep as CUDA graphs, valid
+    // while `key` (window shape, buffers, markers, inflow) is unchanged.
+    cudaGraphExec_t fwd = nullptr, bwd = nullptr;
+    std::vector<double> fwd_key, bwd_key;
     int cap_ck = 0, cap_every = 0;
     int64_t cap_F = 0;
     int cap_mark = 0, cap_band = 0;
@@ -201,6 +206,7 @@ struct btdf_ctx {
     // creation-time inflow speed; btdf_set_inflow changes only cfg.u_in.
     double u_ref = 0.0;
     std::vector<int> band_keys;        // y * nseg + segment of each band segment
+    long long marker_gen = 0;          // bumped by every rebuild of the marker tables
     AdjointTape tape;
     double2* tune_hist = nullptr;      // one-slot force ring used while btdf_autotune times steps
 };
@@ -270,6 +276,9 @@ void free_markers(btdf_ctx* ctx) {
 
 void free_tape(btdf_ctx* ctx) {
     AdjointTape& T = ctx->tape;
+    if (T.fwd) cudaGraphExecDestroy(T.fwd);
+    if (T.bwd) cudaGraphExecDestroy(T.bwd);
+    const long long gen = T.gen;
     dfree(ctx, T.ck);
     dfree(ctx, T.seg);
     dfree(ctx, T.lam[0]);
@@ -287,6 +296,7 @@ void free_tape(btdf_ctx* ctx) {
     dfree(ctx, T.acc);
     ctx->dev_bytes -= T.bytes;
     T = AdjointTape{};
+    T.gen = gen + 1;
 }
 
 bool is_tma(int v) { return v == kVarTma8x2 || v == kVarTma8x3 || v == kVarTma16x2; }
@@ -481,6 +491,7 @@ int read_status(btdf_ctx* ctx) {
 // Static marker data and the node-centric spreading table (Eqs. 14, 15).
 int rebuild_markers(btdf_ctx* ctx) {
     drop_graphs(ctx);
+    ctx->marker_gen++;
     ctx->tape.pending = false;
     ctx->band_keys.clear();
     free_markers(ctx);
@@ -594,7 +605,7 @@ bool tape_pull(const AdjointTape& T, int64_t n) { return !(n == 0 && T.post0); }
 // One forward step of the window: the IB kernel writes F^n into the tape,
 // the LBM kernel spreads it and advances gin -> gout.  No body-force history
 // and no step counter: the context's own state is not touched.
-int tape_step(btdf_ctx* ctx, int64_t n, const float* gin, float* gout) {
+int tape_step(btdf_ctx* ctx, int64_t n, const float* gin, float* gout, cudaStream_t st) {
     AdjointTape& T = ctx->tape;
     const bool pull = tape_pull(T, n);
     float2* F = T.Fall + (size_t)n * ctx->nmark;
@@ -613,18 +624,116 @@ int tape_step(btdf_ctx* ctx, int64_t n, const float* gin, float* gout) {
     q.rhol = T.rhol;
     q.first_pass = 1;
     q.status = ctx->d_status;
-    CK(launch_ib_force(kStoreF32, pull, ctx->width, gin, p, q, ctx->stream));
-    CK(launch_collide_stream(kStoreF32, pull, kVarReg4, gin, gout, p, kFullGrid, true, ctx->stream));
+    CK(launch_ib_force(kStoreF32, pull, ctx->width, gin, p, q, st));
+    CK(launch_collide_stream(kStoreF32, pull, kVarReg4, gin, gout, p, kFullGrid, true, st));
     return BTDF_OK;
 }
 
 // Steps first .. last-1 of segment j.
-int tape_run(btdf_ctx* ctx, int j, int64_t first, int64_t last) {
+int tape_run(btdf_ctx* ctx, int j, int64_t first, int64_t last, cudaStream_t st) {
     const AdjointTape& T = ctx->tape;
     for (int64_t n = first; n < last; n++) {
-        const int rc = tape_step(ctx, n, tape_state(T, j, n), tape_state(T, j, n + 1));
+        const int rc = tape_step(ctx, n, tape_state(T, j, n), tape_state(T, j, n + 1), st);
         if (rc != BTDF_OK) return rc;
     }
+    return BTDF_OK;
+}
+
+// The forward window after its start state: every segment, checkpoints
+// at the segment ends.
+int tape_forward_enqueue(btdf_ctx* ctx, cudaStream_t st) {
+    const AdjointTape& T = ctx->tape;
+    for (int j = 0; j < T.nck; j++) {
+        const int64_t s = (int64_t)j * T.every, e = std::min<int64_t>(s + T.every, T.nsteps);
+        const int rc = tape_run(ctx, j, s, e, st);
+        if (rc != BTDF_OK) return rc;
+    }
+    return BTDF_OK;
+}
+
+// The reverse sweep: segments from the last, each recomputed from its
+// checkpoint, then reversed step by step.
+int tape_backward_enqueue(btdf_ctx* ctx, cudaStream_t st) {
+    AdjointTape& T = ctx->tape;
+    const int nm = ctx->nmark;
+    const size_t sb = sizeof(float) * T.state_elems;
+    CK(cudaMemsetAsync(T.acc, 0, sizeof(double) * (2 * (size_t)nm + 1), st));
+    CK(cudaMemsetAsync(T.lam[0], 0, sb, st));   // dJ/dg^N = 0
+    AdjParams q{};
+    q.nmark = nm;
+    q.nband = (int)ctx->band_keys.size();
+    q.mk = ctx->d_mk;
+    q.aux = ctx->d_aux;
+    q.am = T.am;
+    q.cscale = T.cscale;
+    q.band_keys = T.band_keys;
+    q.fbar_band = T.fbar_band;
+    q.Fbar_band = T.Fbar_band;
+    q.mbar = T.mbar;
+    q.objw = T.objw;
+    q.dJdX = T.acc;
+    q.dJdY = T.acc + nm;
+    q.dU = T.acc + 2 * nm;
+    int c = 0;
+    for (int j = T.nck - 1; j >= 0; j--) {
+        const int64_t s = (int64_t)j * T.every, e = std::min<int64_t>(s + T.every, T.nsteps);
+        // states g^{s+1} .. g^{e-1}; F^{e-1} is already on the tape
+        const int rc = tape_run(ctx, j, s, e - 1, st);
+        if (rc != BTDF_OK) return rc;
+        for (int64_t n = e - 1; n >= s; n--) {
+            LatticeParams p = lattice_params(ctx);
+            p.F = T.Fall + (size_t)n * nm;
+            CK(cudaMemsetAsync(T.lam[1 - c], 0, sb, st));
+            CK(launch_adjoint_step(tape_state(T, j, n), T.lam[c], T.lam[1 - c], p, q, ctx->width,
+                                   tape_pull(T, n), st));
+            c = 1 - c;
+        }
+    }
+    return BTDF_OK;
+}
+
+// Launches one pass of the window through its CUDA graph on the context
+// stream, capturing it first when the window, the buffers, the markers or
+// the inflow changed since the graph was made.
+int tape_graph_launch(btdf_ctx* ctx, bool backward) {
+    AdjointTape& T = ctx->tape;
+    const std::vector<double> key = {(double)T.nsteps, (double)T.every, T.post0 ? 1.0 : 0.0, (double)T.gen,
+                                     (double)ctx->marker_gen, ctx->cfg.u_in};
+    cudaGraphExec_t& exec = backward ? T.bwd : T.fwd;
+    std::vector<double>& have = backward ? T.bwd_key : T.fwd_key;
+    if (!exec || have != key) {
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
+        const int rc = backward ? tape_backward_enqueue(ctx, ctx->cap) : tape_forward_enqueue(ctx, ctx->cap);
+        const cudaError_t e = cudaStreamEndCapture(ctx->cap, &graph);
+        if (rc != BTDF_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+        // Same window shape, new arguments (moved markers, another inflow):
+        // update the instantiated graph in place, which is far cheaper than
+        // instantiating it again.
+        bool updated = false;
+        if (exec) {
+            cudaGraphExecUpdateResultInfo info;
+            updated = cudaGraphExecUpdate(exec, graph, &info) == cudaSuccess;
+            if (!updated) {
+                cudaGetLastError();
+                cudaGraphExecDestroy(exec);
+                exec = nullptr;
+            }
+        }
+        cudaError_t ei = cudaSuccess;
+        if (!updated) ei = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            exec = nullptr;
+            return cuda_fail(ctx, ei, "cudaGraphInstantiate");
+        }
+        have = key;
+    }
+    CK(cudaGraphLaunch(exec, ctx->stream));
     return BTDF_OK;
 }
 
@@ -1234,11 +1343,8 @@ int btdf_adjoint_forward(btdf_ctx* ctx, int64_t nsteps, int32_t every, int32_t b
 
     // forward window from the context's state, checkpoints every `every` steps
     CK(cudaMemcpyAsync(T.ck, ctx->g[ctx->cur], sizeof(float) * T.state_elems, cudaMemcpyDeviceToDevice, st));
-    for (int j = 0; j < nck; j++) {
-        const int64_t s = (int64_t)j * every, e = std::min<int64_t>(s + every, nsteps);
-        rc = tape_run(ctx, j, s, e);
-        if (rc != BTDF_OK) return rc;
-    }
+    rc = tape_graph_launch(ctx, false);
+    if (rc != BTDF_OK) return rc;
     std::vector<float2> F((size_t)nsteps * nm);
     CK(cudaMemcpyAsync(F.data(), T.Fall, sizeof(float2) * F.size(), cudaMemcpyDeviceToHost, st));
     rc = read_status(ctx);
@@ -1264,39 +1370,8 @@ int btdf_adjoint_backward(btdf_ctx* ctx, double* dJdU, double* dJdX, double* dJd
     if (!T.pending) return fail(ctx, BTDF_ESTATE, "no forward window to reverse");
     cudaStream_t st = ctx->stream;
     const int nm = ctx->nmark;
-    const size_t sb = sizeof(float) * T.state_elems;
-    CK(cudaMemsetAsync(T.acc, 0, sizeof(double) * (2 * (size_t)nm + 1), st));
-    CK(cudaMemsetAsync(T.lam[0], 0, sb, st));   // dJ/dg^N = 0
-    AdjParams q{};
-    q.nmark = nm;
-    q.nband = (int)ctx->band_keys.size();
-    q.mk = ctx->d_mk;
-    q.aux = ctx->d_aux;
-    q.am = T.am;
-    q.cscale = T.cscale;
-    q.band_keys = T.band_keys;
-    q.fbar_band = T.fbar_band;
-    q.Fbar_band = T.Fbar_band;
-    q.mbar = T.mbar;
-    q.objw = T.objw;
-    q.dJdX = T.acc;
-    q.dJdY = T.acc + nm;
-    q.dU = T.acc + 2 * nm;
-    int c = 0;
-    for (int j = T.nck - 1; j >= 0; j--) {
-        const int64_t s = (int64_t)j * T.every, e = std::min<int64_t>(s + T.every, T.nsteps);
-        // states g^{s+1} .. g^{e-1}; F^{e-1} is already on the tape
-        const int rc = tape_run(ctx, j, s, e - 1);
-        if (rc != BTDF_OK) return rc;
-        for (int64_t n = e - 1; n >= s; n--) {
-            LatticeParams p = lattice_params(ctx);
-            p.F = T.Fall + (size_t)n * nm;
-            CK(cudaMemsetAsync(T.lam[1 - c], 0, sb, st));
-            CK(launch_adjoint_step(tape_state(T, j, n), T.lam[c], T.lam[1 - c], p, q, ctx->width,
-                                   tape_pull(T, n), st));
-            c = 1 - c;
-        }
-    }
+    const int rg = tape_graph_launch(ctx, true);
+    if (rg != BTDF_OK) return rg;
     std::vector<double> acc(2 * (size_t)nm + 1);
     CK(cudaMemcpyAsync(acc.data(), T.acc, sizeof(double) * acc.size(), cudaMemcpyDeviceToHost, st));
     const int rc = read_status(ctx);
