@@ -80,9 +80,13 @@ typedef enum {
 typedef enum {
     BTDF_BCX_PERIODIC = 0,
     BTDF_BCX_INOUT = 1,      /* inlet + zero-gradient outlet (copy of column nx-2) */
-    BTDF_BCX_CONVECTIVE = 2  /* inlet + convective outlet: d f / dt + u_in d f / dx = 0,
+    BTDF_BCX_CONVECTIVE = 2, /* inlet + convective outlet: d f / dt + u_in d f / dx = 0,
                                 implicit upwind, f(nx-1, t+1) = (f(nx-1, t) + u_in f(nx-2, t+1)) / (1 + u_in);
                                 markers must keep off the outlet column; not for the batch */
+    BTDF_BCX_BOX = 3         /* prescribed-velocity box: every outer node (all four sides) gets
+                                the velocity set by btdf_set_boundary_velocity, by
+                                non-equilibrium extrapolation from its nearest interior node
+                                (Sec. 5.1); bc_y is ignored; not for the batch or the adjoint */
 } btdf_bc_x;
 /* y boundaries: periodic, free-slip walls (half-way specular reflection) or
  * no-slip walls (half-way bounce-back); walls sit half a node outside rows
@@ -144,6 +148,15 @@ int btdf_init_fields(btdf_ctx *ctx, const double *rho, const double *ux, const d
 int btdf_add_markers(btdf_ctx *ctx, int32_t n, const double *X, const double *Y,
                      const double *Ubx, const double *Uby, double ds, double drs,
                      int32_t *body_id);
+
+/* Velocities of the outer nodes of a BTDF_BCX_BOX lattice (the Dirichlet
+ * boundary of the Taylor-Green test, Sec. 5.1), host arrays of
+ * 2 nx + 2 (ny - 2) doubles in perimeter order: row 0 (x = 0..nx-1), row
+ * ny-1 (x = 0..nx-1), column 0 (y = 1..ny-2), column nx-1 (y = 1..ny-2).  The
+ * values apply from the next step on; zero until first set.  Asynchronous on
+ * the context stream (the arrays are read before the call returns).
+ * Errors: ESTATE (no box), EINVAL (null, not finite, |u| >= 0.5). */
+int btdf_set_boundary_velocity(btdf_ctx *ctx, const double *ubx, const double *uby);
 
 /* Adds a circular body: n markers equally spaced on the circle of diameter D
  * about (cx, cy), X_l = cx + (D/2) cos(2 pi l / n), Y_l = cy + (D/2) sin(2 pi l / n),

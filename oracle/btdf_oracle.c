@@ -31,6 +31,9 @@
  *     follows the convective condition d f / dt + U d f / dx = 0 with
  *     U = u_in, implicit upwind in time and space (bc_x = 2); free-slip walls
  *     by half-way specular reflection; no-slip walls by half-way bounce-back.
+ *   - Taylor-Green box (Sec. 5.1, bc_x = 3): every outer node by
+ *     non-equilibrium extrapolation from its nearest interior node (the
+ *     diagonal one at a corner) to the prescribed boundary velocity.
  *
  * Parity pins (tests/test_oracle_*.py): delta identities, equilibrium and
  * Guo-term moments, exact momentum budget, dense-operator brute force,
@@ -65,6 +68,7 @@ typedef struct {
 struct ora_sim {
     int nx, ny, bcx, bcy, delta, nf;
     double *outlet_old;      /* [ny][9] outlet column before the last streaming (bc_x = 2) */
+    double *box_ux, *box_uy; /* perimeter velocities of the prescribed-velocity box (bc_x = 3) */
     double tau, u_in, gx, gy;
     double *f, *fpost;          /* [ny][nx][9] */
     double *rho, *ux, *uy;      /* moments; ux, uy are u* (updated by passes) */
@@ -153,7 +157,7 @@ ora_sim *oracle_create(int nx, int ny, double tau, double u_in, int bc_x, int bc
                        double gx, double gy, int delta, int nf)
 {
     if (nx < 3 || ny < 3 || !(tau > 0.5) || oracle_support_width(delta) == 0 || nf < 1 ||
-        bc_x < 0 || bc_x > 2)
+        bc_x < 0 || bc_x > 3)
         return NULL;
     ora_sim *s = (ora_sim *)calloc(1, sizeof(ora_sim));
     size_t nn = (size_t)nx * ny;
@@ -163,6 +167,8 @@ ora_sim *oracle_create(int nx, int ny, double tau, double u_in, int bc_x, int bc
     s->f = (double *)calloc(nn * 9, sizeof(double));
     s->fpost = (double *)calloc(nn * 9, sizeof(double));
     s->outlet_old = (double *)calloc((size_t)ny * 9, sizeof(double));
+    s->box_ux = (double *)calloc((size_t)(2 * nx + 2 * (ny - 2)), sizeof(double));
+    s->box_uy = (double *)calloc((size_t)(2 * nx + 2 * (ny - 2)), sizeof(double));
     s->rho = (double *)calloc(nn, sizeof(double));
     s->ux = (double *)calloc(nn, sizeof(double));
     s->uy = (double *)calloc(nn, sizeof(double));
@@ -185,7 +191,7 @@ void oracle_destroy(ora_sim *s)
     if (!s) return;
     for (int i = 0; i < s->nb; i++) free_body(&s->b[i]);
     free(s->b);
-    free(s->f); free(s->fpost); free(s->rho); free(s->ux); free(s->uy); free(s->outlet_old);
+    free(s->f); free(s->fpost); free(s->rho); free(s->ux); free(s->uy); free(s->outlet_old); free(s->box_ux); free(s->box_uy);
     free(s->fx); free(s->fy); free(s->dfx); free(s->dfy);
     free(s);
 }
@@ -468,15 +474,56 @@ static void inlet_column(ora_sim *s)
     }
 }
 
+/* Position of outer node (x, y) in the perimeter order: row 0, row ny-1,
+ * column 0 without its corners, column nx-1 without its corners. */
+static int perimeter(const ora_sim *s, int x, int y)
+{
+    if (y == 0) return x;
+    if (y == s->ny - 1) return s->nx + x;
+    if (x == 0) return 2 * s->nx + (y - 1);
+    return 2 * s->nx + (s->ny - 2) + (y - 1);
+}
+
+/* Prescribed-velocity box (Sec. 5.1): every outer node by non-equilibrium
+ * extrapolation from its nearest interior node (the diagonal one at a
+ * corner), f = f_eq(rho_n, u_b) + f_n - f_eq(rho_n, u_n). */
+static void box_nodes(ora_sim *s)
+{
+    const int nx = s->nx, ny = s->ny;
+    double *fn = s->f;
+    for (int y = 0; y < ny; y++)
+        for (int x = 0; x < nx; x++) {
+            if (x != 0 && x != nx - 1 && y != 0 && y != ny - 1) continue;
+            const int xn = x < 1 ? 1 : (x > nx - 2 ? nx - 2 : x);
+            const int yn = y < 1 ? 1 : (y > ny - 2 ? ny - 2 : y);
+            const double *f1 = &fn[((size_t)yn * nx + xn) * 9];
+            double *f0 = &fn[((size_t)y * nx + x) * 9];
+            double r1, u1x, u1y, e_b[9], e_1[9];
+            const int k = perimeter(s, x, y);
+            node_moments(f1, &r1, &u1x, &u1y);
+            oracle_feq(r1, s->box_ux[k], s->box_uy[k], e_b);
+            oracle_feq(r1, u1x, u1y, e_1);
+            for (int a = 0; a < 9; a++) f0[a] = e_b[a] + f1[a] - e_1[a];
+        }
+}
+
+void oracle_set_boundary_velocity(ora_sim *s, const double *ubx, const double *uby)
+{
+    const size_t np = (size_t)(2 * s->nx + 2 * (s->ny - 2));
+    memcpy(s->box_ux, ubx, sizeof(double) * np);
+    memcpy(s->box_uy, uby, sizeof(double) * np);
+}
+
 void oracle_apply_inlet(ora_sim *s)
 {
-    if (s->bcx >= 1) inlet_column(s);
+    if (s->bcx == 1 || s->bcx == 2) inlet_column(s);
 }
 
 static void stream_and_bc(ora_sim *s)
 {
     const int nx = s->nx, ny = s->ny;
-    const int px = s->bcx == 0, py = s->bcy == 0;
+    /* the box overrides every outer node afterwards: stream periodically */
+    const int px = s->bcx == 0 || s->bcx == 3, py = s->bcy == 0 || s->bcx == 3;
     double *fn = s->f;
     /* the outlet column before this streaming (convective outlet) */
     if (s->bcx == 2)
@@ -518,6 +565,8 @@ static void stream_and_bc(ora_sim *s)
         inlet_column(s);
         for (int y = 0; y < ny; y++)          /* outlet: zero gradient */
             for (int a = 0; a < 9; a++) FN(nx - 1, y, a) = FN(nx - 2, y, a);
+    } else if (s->bcx == 3) {
+        box_nodes(s);
     } else if (s->bcx == 2) {
         inlet_column(s);
         /* convective outlet, d f / dt + U d f / dx = 0 with U = u_in,

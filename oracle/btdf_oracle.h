@@ -27,7 +27,9 @@ typedef struct ora_sim ora_sim;
 
 /* bc_x: 0 periodic, 1 inlet (x = 0, velocity u_in) / zero-gradient outlet,
  * 2 the same inlet with a convective outlet (d f / dt + u_in d f / dx = 0,
- * implicit upwind in time and space).
+ * implicit upwind in time and space), 3 a prescribed-velocity box (every
+ * outer node by non-equilibrium extrapolation to the velocity set with
+ * oracle_set_boundary_velocity; bc_y is then ignored).
  * bc_y: 0 periodic, 1 free-slip walls, 2 no-slip walls (half-way bounce-back).
  * delta: 2, 3, 4 (Eqs. 37-39) or 5 (4-point cosine).  nf: forcing passes. */
 ora_sim *oracle_create(int nx, int ny, double tau, double u_in, int bc_x, int bc_y,
@@ -45,6 +47,10 @@ void oracle_set_pops(ora_sim *s, const double *in);
  * simulation with another inlet speed then continues as if that speed had
  * been in force at the last streaming. */
 void oracle_apply_inlet(ora_sim *s);
+/* Outer-node velocities of a bc_x = 3 lattice, 2 nx + 2 (ny - 2) values each
+ * in perimeter order: row 0 (x = 0..nx-1), row ny-1, column 0 (y = 1..ny-2),
+ * column nx-1 (y = 1..ny-2).  Zero until set. */
+void oracle_set_boundary_velocity(ora_sim *s, const double *ubx, const double *uby);
 
 /* One body of n markers; drs <= 0 takes the paper's constant for the delta.
  * Returns the body index. */

@@ -49,6 +49,7 @@ def lib() -> C.CDLL:
     L.oracle_get_pops.argtypes = [vp, _dp]
     L.oracle_set_pops.argtypes = [vp, _dp]
     L.oracle_apply_inlet.argtypes = [vp]
+    L.oracle_set_boundary_velocity.argtypes = [vp, _dp, _dp]
     L.oracle_add_body.restype = C.c_int
     L.oracle_add_body.argtypes = [vp, C.c_int, _dp, _dp, _dp, _dp, C.c_double, C.c_double]
     L.oracle_set_marker_velocity.argtypes = [vp, C.c_int, _dp, _dp]
@@ -182,6 +183,9 @@ class Sim:
 
     def apply_inlet(self):
         lib().oracle_apply_inlet(self._p)
+
+    def set_boundary_velocity(self, ubx, uby):
+        lib().oracle_set_boundary_velocity(self._p, _c(ubx), _c(uby))
 
     def force_field(self):
         sh = (self.ny, self.nx)

@@ -20,7 +20,7 @@ from . import _build
 BTDF_OK, BTDF_EINVAL, BTDF_ENOMEM, BTDF_ECUDA, BTDF_EUNSTABLE, BTDF_ETIMEOUT, BTDF_ESTATE = \
     0, -1, -2, -3, -4, -5, -6
 BTDF_F32, BTDF_F16DEV, BTDF_BF16DEV = 0, 1, 2
-BTDF_BCX_PERIODIC, BTDF_BCX_INOUT, BTDF_BCX_CONVECTIVE = 0, 1, 2
+BTDF_BCX_PERIODIC, BTDF_BCX_INOUT, BTDF_BCX_CONVECTIVE, BTDF_BCX_BOX = 0, 1, 2, 3
 BTDF_BCY_PERIODIC, BTDF_BCY_FREESLIP, BTDF_BCY_NOSLIP = 0, 1, 2
 FIELD_RHO, FIELD_UX, FIELD_UY, FIELD_POPS, FIELD_FX, FIELD_FY = 0, 1, 2, 3, 4, 5
 LAYOUT_PLANES, LAYOUT_ROWS = 0, 1
@@ -38,7 +38,7 @@ EXPORTS = [
     "btdf_batch_sync", "btdf_batch_step_count", "btdf_batch_read_forces", "btdf_batch_read_field",
     "btdf_batch_last_error", "btdf_set_inflow", "btdf_move_markers", "btdf_adjoint_forward",
     "btdf_adjoint_backward", "btdf_adjoint_release", "btdf_autotune", "btdf_batch_autotune",
-    "btdf_read_forces_async", "btdf_add_cylinder",
+    "btdf_read_forces_async", "btdf_add_cylinder", "btdf_set_boundary_velocity",
 ]
 STATIC_MAX_MARKERS = 2048
 VARIANT_COUNT = 11          # collide-stream variants 0 (automatic) .. 10, see btdf_tune
@@ -93,6 +93,7 @@ def lib() -> C.CDLL:
     L.btdf_read_forces.argtypes = [ctxp, C.c_int32, C.c_int64, C.c_int64, vp, vp]
     L.btdf_read_markers.argtypes = [ctxp, C.c_int32, vp, vp, vp, vp]
     L.btdf_read_forces_async.argtypes = [ctxp, C.c_int32, C.c_int64, C.c_int64, vp]
+    L.btdf_set_boundary_velocity.argtypes = [ctxp, _dp, _dp]
     L.btdf_add_cylinder.argtypes = [ctxp, C.c_double, C.c_double, C.c_double, C.c_int32, C.c_double,
                                     C.POINTER(C.c_int32)]
     L.btdf_read_field.argtypes = [ctxp, C.c_int32, vp, C.c_int32]
@@ -249,6 +250,12 @@ class Lattice:
         self._check(rc, "btdf_add_markers")
         self.body_markers.append(n)
         return bid.value
+
+    def set_boundary_velocity(self, ubx, uby):
+        """Outer-node velocities of a BTDF_BCX_BOX lattice, perimeter order
+        (row 0, row ny-1, column 0 without corners, column nx-1 without corners)."""
+        self._check(lib().btdf_set_boundary_velocity(self._ctx, _f64(ubx), _f64(uby)),
+                    "btdf_set_boundary_velocity")
 
     def add_cylinder(self, cx, cy, D, n, drs=0.0) -> int:
         bid = C.c_int32(-1)

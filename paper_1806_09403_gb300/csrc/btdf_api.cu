@@ -172,6 +172,7 @@ struct btdf_ctx {
     unsigned long long* d_step = nullptr;
     int* d_status = nullptr;
     float* d_outlet = nullptr;         // [9][ny] previous outlet column (convective outlet)
+    float2* d_box = nullptr;           // perimeter velocities of the prescribed-velocity box
     std::vector<MarkerAux> aux_host;
     // Pinned host staging, so per-step host <-> device copies are true DMA
     // transfers and a step's inputs and outputs need one synchronization.
@@ -309,8 +310,11 @@ LatticeParams lattice_params(const btdf_ctx* ctx) {
     p.nseg = ctx->nseg;
     p.plane = ctx->plane;
     // the convective outlet is the in/out channel plus an outlet column buffer
-    p.bcx = ctx->cfg.bc_x == BTDF_BCX_CONVECTIVE ? kBcxInout : ctx->cfg.bc_x;
-    p.bcy = ctx->cfg.bc_y;
+    // the box overrides every outer node; its raw pulls wrap like a periodic lattice
+    const bool box = ctx->cfg.bc_x == BTDF_BCX_BOX;
+    p.bcx = box ? kBcxPeriodic : ctx->cfg.bc_x == BTDF_BCX_CONVECTIVE ? kBcxInout : ctx->cfg.bc_x;
+    p.bcy = box ? kBcyPeriodic : ctx->cfg.bc_y;
+    p.box = ctx->d_box;
     p.outlet = ctx->d_outlet;
     p.uc_old = (float)(1.0 / (1.0 + ctx->cfg.u_in));
     p.uc_new = (float)(ctx->cfg.u_in / (1.0 + ctx->cfg.u_in));
@@ -399,6 +403,8 @@ int enqueue_step(btdf_ctx* ctx, cudaStream_t st, bool pull, int cur, bool prof) 
     const bool pdl = ctx->nmark > 0 && !prof;
     int v = ctx->variant == kVarAuto ? (ctx->cfg.storage == kStoreF32 ? kVarReg2 : kVarReg4) : ctx->variant;
     if (is_tma(v) && (!pull || !ctx->tma_ok)) v = kVarReg4;   // TMA kernel pulls only
+    // the box's first and last rows are rebuilt in the register kernels only
+    if (ctx->d_box && (is_tma(v) || v == kVarReg4Pf || v == kVarReg2Pf)) v = kVarReg4;
     if (is_tma(v)) {
         const int grid = ctx->grid_override > 0 ? ctx->grid_override : (int)ctx->tma_grid[v];
         CK(launch_collide_stream_tma(ctx->cfg.storage, v, &ctx->tmap[cur][v == kVarTma16x2 ? 1 : 0],
@@ -833,7 +839,7 @@ int btdf_create(const btdf_config* cfg, void* stream, btdf_ctx** out) {
     if (support_width(c.delta) == 0) return BTDF_EINVAL;
     if (c.nf < 1 || c.nf > 64) return BTDF_EINVAL;
     if (c.storage < 0 || c.storage > 2) return BTDF_EINVAL;
-    if (c.bc_x < 0 || c.bc_x > 2 || c.bc_y < 0 || c.bc_y > 2) return BTDF_EINVAL;
+    if (c.bc_x < 0 || c.bc_x > 3 || c.bc_y < 0 || c.bc_y > 2) return BTDF_EINVAL;
     if (c.history_len < 1) return BTDF_EINVAL;
     if (c.layout != BTDF_LAYOUT_PLANES && c.layout != BTDF_LAYOUT_ROWS) return BTDF_EINVAL;
     if (!std::isfinite(c.u_in) || std::fabs(c.u_in) >= 0.5) return BTDF_EINVAL;
@@ -886,7 +892,10 @@ int btdf_create(const btdf_config* cfg, void* stream, btdf_ctx** out) {
     *ctx->status_pin = 0;
     if (dalloc(ctx, &ctx->d_step, sizeof(unsigned long long)) != cudaSuccess ||
         dalloc(ctx, &ctx->d_status, sizeof(int)) != cudaSuccess ||
-        (c.bc_x == BTDF_BCX_CONVECTIVE && dalloc(ctx, &ctx->d_outlet, sizeof(float) * 9 * c.ny) != cudaSuccess))
+        (c.bc_x == BTDF_BCX_CONVECTIVE && dalloc(ctx, &ctx->d_outlet, sizeof(float) * 9 * c.ny) != cudaSuccess) ||
+        (c.bc_x == BTDF_BCX_BOX && dalloc(ctx, &ctx->d_box, sizeof(float2) * (2 * c.nx + 2 * (c.ny - 2))) != cudaSuccess))
+        return bail(BTDF_ECUDA);
+    if (ctx->d_box && cudaMemsetAsync(ctx->d_box, 0, sizeof(float2) * (2 * c.nx + 2 * (c.ny - 2)), ctx->stream) != cudaSuccess)
         return bail(BTDF_ECUDA);
     if (cudaMemsetAsync(ctx->d_step, 0, sizeof(unsigned long long), ctx->stream) != cudaSuccess ||
         cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream) != cudaSuccess ||
@@ -907,6 +916,7 @@ int btdf_destroy(btdf_ctx* ctx) {
     dfree(ctx, ctx->d_step);
     dfree(ctx, ctx->d_status);
     dfree(ctx, ctx->d_outlet);
+    dfree(ctx, ctx->d_box);
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
     for (cudaEvent_t e : ctx->aux_ev)
         if (e) cudaEventDestroy(e);
@@ -1000,6 +1010,22 @@ int btdf_add_cylinder(btdf_ctx* ctx, double cx, double cy, double D, int32_t n, 
         Y[l] = cy + 0.5 * D * std::sin(th);
     }
     return btdf_add_markers(ctx, n, X.data(), Y.data(), nullptr, nullptr, M_PI * D / (double)n, drs, body_id);
+}
+
+int btdf_set_boundary_velocity(btdf_ctx* ctx, const double* ubx, const double* uby) {
+    if (!ctx) return BTDF_EINVAL;
+    if (!ctx->d_box) return fail(ctx, BTDF_ESTATE, "the lattice has no prescribed-velocity box");
+    if (!ubx || !uby) return fail(ctx, BTDF_EINVAL, "null boundary velocity");
+    const int np = 2 * ctx->cfg.nx + 2 * (ctx->cfg.ny - 2);
+    std::vector<float2> v(np);
+    for (int k = 0; k < np; k++) {
+        if (!std::isfinite(ubx[k]) || !std::isfinite(uby[k]) || std::fabs(ubx[k]) >= 0.5 || std::fabs(uby[k]) >= 0.5)
+            return fail(ctx, BTDF_EINVAL, "boundary velocity not finite or not below 0.5");
+        v[k] = make_float2((float)ubx[k], (float)uby[k]);
+    }
+    // pageable source: the call returns once the runtime has staged it
+    CK(cudaMemcpyAsync(ctx->d_box, v.data(), sizeof(float2) * np, cudaMemcpyHostToDevice, ctx->stream));
+    return BTDF_OK;
 }
 
 int btdf_set_marker_velocity(btdf_ctx* ctx, int32_t body, const double* Ubx, const double* Uby) {
@@ -1286,8 +1312,8 @@ int btdf_adjoint_forward(btdf_ctx* ctx, int64_t nsteps, int32_t every, int32_t b
     if (ctx->nmark == 0) return fail(ctx, BTDF_ESTATE, "the objective needs at least one body");
     if (ctx->cfg.nf != 1 || ctx->cfg.storage != BTDF_F32)
         return fail(ctx, BTDF_EINVAL, "the adjoint supports nf = 1 with FP32 storage");
-    if (ctx->cfg.bc_x == BTDF_BCX_CONVECTIVE)
-        return fail(ctx, BTDF_EINVAL, "the adjoint supports the zero-gradient outlet only");
+    if (ctx->cfg.bc_x == BTDF_BCX_CONVECTIVE || ctx->cfg.bc_x == BTDF_BCX_BOX)
+        return fail(ctx, BTDF_EINVAL, "the adjoint supports periodic and in/out (zero-gradient) x boundaries only");
     if (nsteps < 1 || every < 1 || nsteps > (1ll << 30))
         return fail(ctx, BTDF_EINVAL, "need nsteps >= 1 and every >= 1");
     if (!(dref > 0.0) || !std::isfinite(dref)) return fail(ctx, BTDF_EINVAL, "need dref > 0");

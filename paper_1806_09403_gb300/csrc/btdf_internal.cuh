@@ -38,6 +38,16 @@ __host__ __device__ constexpr int opposite(int a) {
 }
 
 enum : int { kBcxPeriodic = 0, kBcxInout = 1 };
+
+// Index of outer node (x, y) in the perimeter order of the prescribed-velocity
+// box: row 0 (x = 0..nx-1), row ny-1 (x = 0..nx-1), column 0 (y = 1..ny-2),
+// column nx-1 (y = 1..ny-2); 2 nx + 2 (ny - 2) entries.
+__host__ __device__ inline int perimeter_index(int x, int y, int nx, int ny) {
+    if (y == 0) return x;
+    if (y == ny - 1) return nx + x;
+    if (x == 0) return 2 * nx + (y - 1);
+    return 2 * nx + (ny - 2) + (y - 1);
+}
 enum : int { kBcyPeriodic = 0, kBcyFreeslip = 1, kBcyNoslip = 2 };
 enum : int { kStoreF32 = 0, kStoreF16 = 1, kStoreBF16 = 2 };
 
@@ -92,6 +102,10 @@ struct LatticeParams {
     // weights of f(N, t+1) = old / (1 + U) + U / (1 + U) f(N-1, t+1).
     float* outlet;
     float uc_old, uc_new;
+    // Prescribed-velocity box (null: none): every outer node gets the
+    // velocity box[perimeter_index(x, y)] by non-equilibrium extrapolation
+    // from its nearest interior node.
+    const float2* box;
     const int* seg_index;      // [ny * nseg] band segment id or -1 (null: no band)
     const int* seg_ptr;        // [nband * (kSeg + 1)] CSR row pointers per node
     const CsrEntry* csr;

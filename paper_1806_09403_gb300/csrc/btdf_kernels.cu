@@ -295,6 +295,18 @@ __device__ __forceinline__ void lbm_segment(const T* __restrict__ gin, T* __rest
             }
         }
     }
+    if (kPull && p.box != nullptr && live && (y == 0 || y == p.ny - 1)) {
+        // prescribed-velocity box: every node of the first and last rows
+#pragma unroll
+        for (int i = 0; i < NPL; i++) {
+            if (x0 + i < p.nx) {
+                float fe[9];
+                pull_node<T>(gin, p, x0 + i, y, fe);
+#pragma unroll
+                for (int a = 0; a < 9; a++) f[a][i] = fe[a];
+            }
+        }
+    }
     if (kPull && live && x0 < p.nx && (x0 == 0 || x0 + NPL - 1 >= p.nx - 1)) {
 #pragma unroll
         for (int i = 0; i < NPL; i++) {

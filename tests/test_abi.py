@@ -45,7 +45,7 @@ def test_version_and_status_strings():
 
 @pytest.mark.parametrize("field,value", [
     ("tau", 0.5), ("tau", float("nan")), ("nx", 3), ("ny", 0), ("delta", 1), ("delta", 6),
-    ("nf", 0), ("nf", 65), ("storage", 3), ("bc_x", 3), ("bc_y", 3), ("history_len", 0),
+    ("nf", 0), ("nf", 65), ("storage", 3), ("bc_x", 4), ("bc_y", 3), ("history_len", 0),
     ("u_in", float("inf")), ("u_in", 0.6), ("gx", float("nan")), ("layout", 2),
 ])
 def test_invalid_config_rejected_on_host(field, value):

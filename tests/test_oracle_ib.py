@@ -195,3 +195,39 @@ def test_btdf_single_pass_against_mdf_four_passes():
     df = _slip(1.0, steps=200, nf=1)
     assert btdf <= mdf4, (btdf, mdf4)
     assert btdf < 0.35 * df, (btdf, df)
+
+
+def _tg_circle(N, T=1.0):
+    """Sec. 5.1: the Taylor-Green vortex in the box [-L, L]^2 with a circle of
+    diameter L at its centre whose markers carry the exact velocity
+    (Eqs. 40-41 at the time of the state they act on); returns the Eq. 43
+    errors of the velocity field and of the corrected marker velocity."""
+    tg = W.TaylorGreenBox(N)
+    s = O.Sim(tg.n, tg.n, tg.tau, 0.0, W.BCX_BOX, 0, 0.0, 0.0, 3, 1)
+    s.init_fields(*tg.fields(0.0))
+    b = tg.circle()
+    s.add_body(b.X, b.Y, b.ds)
+    K = tg.steps_to(T)
+    for k in range(1, K + 1):
+        s.set_boundary_velocity(*tg.boundary(k))
+        s.set_marker_velocity(0, *tg.marker_velocity(b, k - 1))
+        s.step(1)
+    _, ux, uy = s.moments()
+    X, Y = tg.coords()
+    ax, ay = tg.velocity(X, Y, K)
+    e = math.sqrt((((ux - ax) ** 2 + (uy - ay) ** 2).sum()) / ((ax ** 2 + ay ** 2).sum()))
+    d = s.marker_diag(0)
+    bx, by = tg.marker_velocity(b, K - 1)
+    eb = math.sqrt((((d["Ux"] - bx) ** 2 + (d["Uy"] - by) ** 2).sum()) / ((bx ** 2 + by ** 2).sum()))
+    return e, eb
+
+
+def test_taylor_green_with_circle_second_order():
+    """Fig. 5: with the exact solution on the outer box and on the circle,
+    the overall and the boundary velocity errors of BTDF converge at about
+    second order (N = 10, 20, 40 to T = 1, Re = 10, tau = 0.65)."""
+    e = [_tg_circle(N) for N in (10, 20, 40)]
+    for (a, ab), (b, bb) in zip(e[:-1], e[1:]):
+        assert 1.7 < math.log2(a / b) < 2.4, e
+        assert math.log2(ab / bb) > 1.7, e
+

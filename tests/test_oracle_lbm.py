@@ -216,6 +216,44 @@ def test_convective_outlet_relaxes_towards_its_neighbour():
     assert not np.array_equal(f[:, -1, :], z.pops()[:, -1, :])   # not the zero-gradient copy
 
 
+def _tg_box_error(N, T=0.5):
+    tg = W.TaylorGreenBox(N)
+    s = O.Sim(tg.n, tg.n, tg.tau, 0.0, W.BCX_BOX, 0, 0.0, 0.0, 3, 1)
+    s.init_fields(*tg.fields(0.0))
+    K = tg.steps_to(T)
+    for k in range(1, K + 1):
+        s.set_boundary_velocity(*tg.boundary(k))   # the boundary at the time the step reaches
+        s.step(1)
+    _, ux, uy = s.moments()
+    X, Y = tg.coords()
+    ax, ay = tg.velocity(X, Y, K)
+    return math.sqrt((((ux - ax) ** 2 + (uy - ay) ** 2).sum()) / ((ax ** 2 + ay ** 2).sum()))
+
+
+def test_taylor_green_box_second_order():
+    """Sec. 5.1 without the circle: the decaying vortex (Eqs. 40-42) in the
+    box [-L, L]^2 whose outer nodes carry the exact velocity by
+    non-equilibrium extrapolation converges at second order (Eq. 43 error
+    ratio ~4 per halving of dh)."""
+    e = [_tg_box_error(N) for N in (8, 16, 32)]
+    r1, r2 = e[0] / e[1], e[1] / e[2]
+    assert 3.3 < r1 < 4.6 and 3.3 < r2 < 4.6, (e, r1, r2)
+
+
+def test_box_keeps_a_uniform_flow():
+    """A uniform flow whose velocity is also prescribed on the box stays
+    exactly uniform."""
+    n, u = 12, (0.03, -0.02)
+    s = O.Sim(n, n, 0.7, 0.0, W.BCX_BOX, 0, 0.0, 0.0, 3, 1)
+    s.init_fields(np.ones((n, n)), np.full((n, n), u[0]), np.full((n, n), u[1]))
+    px, _ = W.perimeter_nodes(n, n)
+    s.set_boundary_velocity(np.full(len(px), u[0]), np.full(len(px), u[1]))
+    s.step(40)
+    r, ux, uy = s.moments()
+    assert np.abs(r - 1).max() < 1e-14
+    assert np.abs(ux - u[0]).max() < 1e-14 and np.abs(uy - u[1]).max() < 1e-14
+
+
 def _poiseuille(tau, ny=16, g=1e-6, steps=None):
     nu = (tau - 0.5) / 3.0
     if steps is None:

@@ -31,6 +31,7 @@ import numpy as np
 BCX_PERIODIC = 0
 BCX_INOUT = 1
 BCX_CONVECTIVE = 2
+BCX_BOX = 3
 BCY_PERIODIC = 0
 BCY_FREESLIP = 1
 BCY_NOSLIP = 2
@@ -227,3 +228,73 @@ def taylor_green_fields(n: int, u0: float):
     ux = -u0 * np.cos(np.pi * X / L) * np.sin(np.pi * Y / L)
     uy = u0 * np.sin(np.pi * X / L) * np.cos(np.pi * Y / L)
     return np.ones((n, n)), ux, uy
+
+
+def perimeter_nodes(nx: int, ny: int):
+    """Outer nodes of an nx x ny lattice in the order the prescribed-velocity
+    box takes its boundary velocities: row 0, row ny-1, column 0 without its
+    corners, column nx-1 without its corners.  Returns (x, y) int arrays."""
+    xs = [np.arange(nx), np.arange(nx), np.zeros(ny - 2, int), np.full(ny - 2, nx - 1)]
+    ys = [np.zeros(nx, int), np.full(nx, ny - 1), np.arange(1, ny - 1), np.arange(1, ny - 1)]
+    return np.concatenate(xs), np.concatenate(ys)
+
+
+@dataclass
+class TaylorGreenBox:
+    """The decaying Taylor-Green vortex of Sec. 5.1 on [-L, L]^2 with L = N
+    lattice units (dh = L / N): 2N + 1 nodes per side at x_i = -L + i, the
+    outer ones on the box.  Re = u0 L / nu = 10 and tau = 0.65 as in the
+    paper, so u0 = Re nu / L; T = u0 t / L = 1 is reached after 2 N^2 steps.
+    Optionally a circle of diameter L at the centre, ds = dh."""
+    N: int
+    re: float = 10.0
+    tau: float = 0.65
+
+    @property
+    def n(self) -> int:
+        return 2 * self.N + 1
+
+    @property
+    def nu(self) -> float:
+        return (self.tau - 0.5) / 3.0
+
+    @property
+    def u0(self) -> float:
+        return self.re * self.nu / self.N
+
+    def steps_to(self, T: float) -> int:
+        return int(round(T * self.N / self.u0))
+
+    def coords(self):
+        c = np.arange(self.n, dtype=np.float64) - self.N
+        return np.meshgrid(c, c)
+
+    def velocity(self, x, y, t):
+        """Eqs. 40-41 at lattice time t."""
+        L, k = float(self.N), np.exp(-2.0 * np.pi ** 2 * self.nu * t / self.N ** 2)
+        ux = -self.u0 * np.cos(np.pi * x / L) * np.sin(np.pi * y / L) * k
+        uy = self.u0 * np.sin(np.pi * x / L) * np.cos(np.pi * y / L) * k
+        return ux, uy
+
+    def density(self, x, y, t):
+        """Eq. 42 read with cos(2 pi y / L) (the printed sin is taken for a
+        typo), c_s^2 = 1/3."""
+        L, k = float(self.N), np.exp(-4.0 * np.pi ** 2 * self.nu * t / self.N ** 2)
+        return 1.0 - 0.75 * self.u0 ** 2 * (np.cos(2 * np.pi * x / L) + np.cos(2 * np.pi * y / L)) * k
+
+    def fields(self, t=0.0):
+        X, Y = self.coords()
+        ux, uy = self.velocity(X, Y, t)
+        return self.density(X, Y, t), ux, uy
+
+    def boundary(self, t):
+        px, py = perimeter_nodes(self.n, self.n)
+        return self.velocity(px - float(self.N), py - float(self.N), t)
+
+    def circle(self) -> Body:
+        m = max(8, int(round(np.pi * self.N)))
+        return circle_markers(float(self.N), float(self.N), float(self.N), m)
+
+    def marker_velocity(self, body: Body, t):
+        return self.velocity(body.X - self.N, body.Y - self.N, t)
+
