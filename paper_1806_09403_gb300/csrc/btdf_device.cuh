@@ -209,29 +209,36 @@ __device__ void pull_raw(const T* __restrict__ g, const LatticeParams& p, int x,
     }
 }
 
-// Post-streaming deviations with every boundary rule: inlet column by
-// non-equilibrium extrapolation from column 1 to u = (u_in, 0),
+// Post-streaming deviations with the boundary rules of the x ends: inlet
+// column by non-equilibrium extrapolation from column 1 to u = (u_in, 0),
 // f(0) = f(1) + f_eq(rho_1, u_in) - f_eq(rho_1, u*_1); outlet column copied
 // from column nx-2, or, with the convective outlet, relaxed towards it from
-// the previous step's outlet column; with a prescribed-velocity box, every
-// outer node by the same extrapolation to its own boundary velocity.
+// the previous step's outlet column.  The prescribed-velocity box is applied
+// by read_node and, in the LBM kernels, by box_override.
+// Prescribed-velocity box: outer node (x, y) by extrapolation from the
+// nearest interior node (the diagonal one at corners) to the node's boundary
+// velocity.  Kept out of line: the box is a test configuration, and inlining
+// it into every row-end path of the LBM kernels overflows the instruction
+// cache of the common path.
+template <typename T>
+__device__ __noinline__ void pull_box_node(const T* __restrict__ g, const LatticeParams& p, int x, int y,
+                                           float* f) {
+    const int xn = min(max(x, 1), p.nx - 2), yn = min(max(y, 1), p.ny - 2);
+    float f1[9];
+    pull_raw<T>(g, p, xn, yn, f1);
+    const Moments m = moments(f1, p.urx, p.ury);
+    const float2 ub = p.box[perimeter_index(x, y, p.nx, p.ny)];
+    const float inx = ub.x - p.urx, iny = ub.y - p.ury;
+#pragma unroll
+    for (int a = 0; a < 9; a++)
+        f[a] = f1[a] + wt(a) * m.rho *
+                           (eq_part_diff(a, p.urx, p.ury, inx, iny) -
+                            eq_part_diff(a, p.urx, p.ury, m.dux, m.duy));
+}
+
 template <typename T>
 __device__ void pull_node(const T* __restrict__ g, const LatticeParams& p, int x, int y, float f[9]) {
-    if (p.box != nullptr && (x == 0 || x == p.nx - 1 || y == 0 || y == p.ny - 1)) {
-        // prescribed-velocity box: extrapolation from the nearest interior
-        // node (the diagonal one at corners) to the node's boundary velocity
-        const int xn = min(max(x, 1), p.nx - 2), yn = min(max(y, 1), p.ny - 2);
-        float f1[9];
-        pull_raw<T>(g, p, xn, yn, f1);
-        const Moments m = moments(f1, p.urx, p.ury);
-        const float2 ub = p.box[perimeter_index(x, y, p.nx, p.ny)];
-        const float inx = ub.x - p.urx, iny = ub.y - p.ury;
-#pragma unroll
-        for (int a = 0; a < 9; a++)
-            f[a] = f1[a] + wt(a) * m.rho *
-                               (eq_part_diff(a, p.urx, p.ury, inx, iny) -
-                                eq_part_diff(a, p.urx, p.ury, m.dux, m.duy));
-    } else if (p.bcx == kBcxInout && x == 0) {
+    if (p.bcx == kBcxInout && x == 0) {
         float f1[9];
         pull_raw<T>(g, p, 1, y, f1);
         const Moments m = moments(f1, p.urx, p.ury);
@@ -258,7 +265,10 @@ template <typename T>
 __device__ __forceinline__ void read_node(const T* __restrict__ g, const LatticeParams& p, bool pull,
                                           int x, int y, float f[9]) {
     if (pull) {
-        pull_node<T>(g, p, x, y, f);
+        if (p.box != nullptr && (x == 0 || x == p.nx - 1 || y == 0 || y == p.ny - 1))
+            pull_box_node<T>(g, p, x, y, f);
+        else
+            pull_node<T>(g, p, x, y, f);
     } else {
 #pragma unroll
         for (int a = 0; a < 9; a++) f[a] = Io<T>::ld1(g + p.poff[a] + (unsigned)y * p.rs + (unsigned)x);

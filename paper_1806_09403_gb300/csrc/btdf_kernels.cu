@@ -295,19 +295,22 @@ __device__ __forceinline__ void lbm_segment(const T* __restrict__ gin, T* __rest
             }
         }
     }
-    if (kPull && p.box != nullptr && live && (y == 0 || y == p.ny - 1)) {
-        // prescribed-velocity box: every node of the first and last rows
+    if (kPull && p.box != nullptr) {
+        // prescribed-velocity box: the lane's outer nodes (the first and last
+        // rows, the two end columns), each through one out-of-line call
+        if (live && (y == 0 || y == p.ny - 1 || x0 == 0 || x0 + NPL - 1 >= p.nx - 1)) {
 #pragma unroll
-        for (int i = 0; i < NPL; i++) {
-            if (x0 + i < p.nx) {
-                float fe[9];
-                pull_node<T>(gin, p, x0 + i, y, fe);
+            for (int i = 0; i < NPL; i++) {
+                const int x = x0 + i;
+                if (x < p.nx && (y == 0 || y == p.ny - 1 || x == 0 || x == p.nx - 1)) {
+                    float fe[9];
+                    pull_box_node<T>(gin, p, x, y, fe);
 #pragma unroll
-                for (int a = 0; a < 9; a++) f[a][i] = fe[a];
+                    for (int a = 0; a < 9; a++) f[a][i] = fe[a];
+                }
             }
         }
-    }
-    if (kPull && live && x0 < p.nx && (x0 == 0 || x0 + NPL - 1 >= p.nx - 1)) {
+    } else if (kPull && live && x0 < p.nx && (x0 == 0 || x0 + NPL - 1 >= p.nx - 1)) {
 #pragma unroll
         for (int i = 0; i < NPL; i++) {
             const int x = x0 + i;
