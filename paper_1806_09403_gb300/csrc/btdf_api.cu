@@ -332,8 +332,8 @@ LatticeParams lattice_params(const btdf_ctx* ctx) {
             p.eur[a] = (float)eU;
             p.c1[a] = (float)(3.0 + 9.0 * eU);
             p.kr[a] = (float)(1.0 + 3.0 * eU + 4.5 * eU * eU - 1.5 * (Ux * Ux + Uy * Uy));
-            p.wom[a] = (float)(w / tau);
-            p.wg[a] = (float)(w * (1.0 - 0.5 / tau));
+            p.wom[a] = (float)(w / tau * store_scale(ctx->cfg.storage));
+            p.wg[a] = (float)(w * (1.0 - 0.5 / tau) * store_scale(ctx->cfg.storage));
         }
     }
     p.nwork = (long long)ctx->cfg.ny * ctx->nseg;

@@ -144,8 +144,8 @@ LatticeParams base_params(const btdf_batch* bt, int c) {
         p.eur[a] = (float)eU;
         p.c1[a] = (float)(3.0 + 9.0 * eU);
         p.kr[a] = (float)(1.0 + 3.0 * eU + 4.5 * eU * eU - 1.5 * (Ux * Ux + Uy * Uy));
-        p.wom[a] = (float)(w / k.tau);
-        p.wg[a] = (float)(w * (1.0 - 0.5 / k.tau));
+        p.wom[a] = (float)(w / k.tau * store_scale(bt->storage));
+        p.wg[a] = (float)(w * (1.0 - 0.5 / k.tau) * store_scale(bt->storage));
     }
     p.gx = (float)k.gx;
     p.gy = (float)k.gy;

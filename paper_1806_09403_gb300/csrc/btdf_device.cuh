@@ -48,7 +48,7 @@ template <typename H, typename H2> struct Io16 {
 // 1e-6 .. 1e-3 away from the reference equilibrium, where unscaled FP16 would
 // be subnormal; the largest deviations (~0.1 near a body at start-up) stay far
 // below FP16's range after scaling.  Power-of-two scaling is exact.
-constexpr float kHalfScale = 1024.0f;
+constexpr float kHalfScale = kF16Scale;
 constexpr float kHalfInvScale = 1.0f / 1024.0f;
 template <> __device__ __forceinline__ float2 Io16<__half, __half2>::to2(unsigned u) {
     const float2 v = __half22float2(*reinterpret_cast<const __half2*>(&u));
@@ -116,6 +116,51 @@ template <> __device__ __forceinline__ float IoHalf<__nv_bfloat16, __nv_bfloat16
 template <> struct Io<__half> : IoHalf<__half, __half2> {};
 template <> struct Io<__nv_bfloat16> : IoHalf<__nv_bfloat16, __nv_bfloat162> {};
 
+// Stored-scale access for the LBM kernels: populations exactly as stored,
+// so FP16 keeps its 2^10 factor.  Those kernels carry the factor through the
+// streaming and fold it into the moments and the collision constants instead
+// of scaling every population on the way in and out; kScale is the stored
+// value of a unit deviation.  Power-of-two scaling is exact, so the results
+// are the same as with the scaled access.
+template <typename T> struct Raw : Io<T> {
+    static constexpr float kScale = 1.0f;
+};
+template <> struct Raw<__half> {
+    static constexpr float kScale = kHalfScale;
+    static __device__ __forceinline__ float2 to2(unsigned u) {
+        return __half22float2(*reinterpret_cast<const __half2*>(&u));
+    }
+    static __device__ __forceinline__ unsigned from2(float a, float b) {
+        const __half2 h = __floats2half2_rn(a, b);
+        return *reinterpret_cast<const unsigned*>(&h);
+    }
+    template <int N>
+    static __device__ __forceinline__ void ldv(const __half* p, float (&o)[N]) {
+        if constexpr (N == 4) {
+            const uint2 r = *reinterpret_cast<const uint2*>(p);
+            const float2 a = to2(r.x), b = to2(r.y);
+            o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+        } else if constexpr (N == 1) {
+            o[0] = __half2float(*p);
+        } else {
+            const float2 a = to2(*reinterpret_cast<const unsigned*>(p));
+            o[0] = a.x; o[1] = a.y;
+        }
+    }
+    template <int N>
+    static __device__ __forceinline__ void stv(__half* p, const float (&o)[N]) {
+        if constexpr (N == 4) {
+            *reinterpret_cast<uint2*>(p) = make_uint2(from2(o[0], o[1]), from2(o[2], o[3]));
+        } else if constexpr (N == 1) {
+            *p = __float2half_rn(o[0]);
+        } else {
+            *reinterpret_cast<unsigned*>(p) = from2(o[0], o[1]);
+        }
+    }
+    static __device__ __forceinline__ float ld1(const __half* p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ float ld1s(const __half* p) { return __half2float(*p); }
+};
+
 template <typename T>
 __device__ __forceinline__ void store_scalar(T* p, float v);
 template <> __device__ __forceinline__ void store_scalar<float>(float* p, float v) { *p = v; }
@@ -153,13 +198,15 @@ struct Moments {
 // Every product that meets a sum is written as an explicit rounded operation
 // (__fmaf_rn, __fmul_rn), so the compiler cannot contract differently in
 // different kernels and all launch shapes give bitwise identical results.
-__device__ __forceinline__ Moments moments(const float d[9], float urx, float ury) {
+// d may hold the deviations times a power of two; s (its inverse, a
+// compile-time constant at every call) scales the sums back exactly.
+__device__ __forceinline__ Moments moments(const float d[9], float urx, float ury, float s = 1.0f) {
     Moments m;
-    m.drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
+    m.drho = (((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8]) * s;
     m.rho = 1.0f + m.drho;
     m.inv = __fdividef(1.0f, m.rho);
-    const float jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
-    const float jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
+    const float jx = ((d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7])) * s;
+    const float jy = ((d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8])) * s;
     m.dux = __fmul_rn(__fmaf_rn(-m.drho, urx, jx), m.inv);
     m.duy = __fmul_rn(__fmaf_rn(-m.drho, ury, jy), m.inv);
     return m;
@@ -209,12 +256,6 @@ __device__ void pull_raw(const T* __restrict__ g, const LatticeParams& p, int x,
     }
 }
 
-// Post-streaming deviations with the boundary rules of the x ends: inlet
-// column by non-equilibrium extrapolation from column 1 to u = (u_in, 0),
-// f(0) = f(1) + f_eq(rho_1, u_in) - f_eq(rho_1, u*_1); outlet column copied
-// from column nx-2, or, with the convective outlet, relaxed towards it from
-// the previous step's outlet column.  The prescribed-velocity box is applied
-// by read_node and, in the LBM kernels, by box_override.
 // Prescribed-velocity box: outer node (x, y) by extrapolation from the
 // nearest interior node (the diagonal one at corners) to the node's boundary
 // velocity.  Kept out of line: the box is a test configuration, and inlining
@@ -236,6 +277,12 @@ __device__ __noinline__ void pull_box_node(const T* __restrict__ g, const Lattic
                             eq_part_diff(a, p.urx, p.ury, m.dux, m.duy));
 }
 
+// Post-streaming deviations with the boundary rules of the x ends: inlet
+// column by non-equilibrium extrapolation from column 1 to u = (u_in, 0),
+// f(0) = f(1) + f_eq(rho_1, u_in) - f_eq(rho_1, u*_1); outlet column copied
+// from column nx-2, or, with the convective outlet, relaxed towards it from
+// the previous step's outlet column.  The prescribed-velocity box is applied
+// by read_node and by the LBM kernels through pull_box_node.
 template <typename T>
 __device__ void pull_node(const T* __restrict__ g, const LatticeParams& p, int x, int y, float f[9]) {
     if (p.bcx == kBcxInout && x == 0) {

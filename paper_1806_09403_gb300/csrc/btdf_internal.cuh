@@ -25,6 +25,15 @@ __host__ __device__ constexpr int ex(int a) {
 __host__ __device__ constexpr int ey(int a) {
     return (a == 2 || a == 5 || a == 6) ? 1 : ((a == 4 || a == 7 || a == 8) ? -1 : 0);
 }
+// e_a . (x, y), leaving out the zero components: IEEE arithmetic keeps a
+// 0 * x term, so writing ex(a) * x + ey(a) * y costs an instruction per axis
+// population for nothing.  The value is the same (one rounding of the exact
+// sum for the diagonals).
+__host__ __device__ constexpr float edot(int a, float x, float y) {
+    return ex(a) == 0 ? (ey(a) == 0 ? 0.0f : (ey(a) > 0 ? y : -y))
+                      : (ey(a) == 0 ? (ex(a) > 0 ? x : -x)
+                                    : (ex(a) > 0 ? x : -x) + (ey(a) > 0 ? y : -y));
+}
 __host__ __device__ constexpr float wt(int a) {
     return a == 0 ? 4.0f / 9.0f : (a < 5 ? 1.0f / 9.0f : 1.0f / 36.0f);
 }
@@ -50,6 +59,10 @@ __host__ __device__ inline int perimeter_index(int x, int y, int nx, int ny) {
 }
 enum : int { kBcyPeriodic = 0, kBcyFreeslip = 1, kBcyNoslip = 2 };
 enum : int { kStoreF32 = 0, kStoreF16 = 1, kStoreBF16 = 2 };
+// FP16 storage holds the deviations times 2^10 (see Io<__half>).
+constexpr float kF16Scale = 1024.0f;
+// Stored value of a unit deviation for a storage format.
+inline double store_scale(int storage) { return storage == kStoreF16 ? (double)kF16Scale : 1.0; }
 
 // Static per-marker data evaluated once on the host in FP64 (Eq. 14):
 // support node coordinates (wrapped on periodic axes, clamped and given zero
@@ -83,6 +96,11 @@ struct LatticeParams {
     long long plane;           // elements per population plane (nxp * ny)
     unsigned rs;               // elements between consecutive rows of one plane
     long long nwork;           // warp row segments of the LBM kernel
+    // Warp-to-segment map of the register LBM kernels, set for each launch:
+    // warp w starts at row w / nsegw, computed as (umulhi(w, wmul) + w) >> wshift,
+    // and steps wdy rows plus wds segments per grid stride.
+    unsigned wmul;
+    int wshift, wdy, wds;
     unsigned poff[9];          // element offset of population plane a (row 0, x 0)
     int bcx, bcy;
     float omega;               // 1 / tau
@@ -94,7 +112,9 @@ struct LatticeParams {
     // of the flow from the free stream rather than with the flow itself.
     float urx, ury;
     // Per-population constants of the collision in that form:
-    //   c1 = 3 + 9 e.U_r,  k = 1 + P_a(U_r),  wom = w_a / tau,  wg = w_a (1 - 1/(2 tau)).
+    //   c1 = 3 + 9 e.U_r,  k = 1 + P_a(U_r),  wom = w_a / tau,  wg = w_a (1 - 1/(2 tau)),
+    // wom and wg times the storage scale (2^10 for FP16, else 1): the LBM
+    // kernels collide the populations at their stored scale.
     float eur[9], c1[9], kr[9], wom[9], wg[9];
     float gx, gy;              // uniform body force
     // Convective outlet (null: zero-gradient): the outlet column's

@@ -88,7 +88,7 @@ __device__ __forceinline__ void collide_store(float (&f)[9][NPL], T* __restrict_
 #pragma unroll
             for (int k = 1; k < NPL; k++)
                 if (k == i) v = f[a][k];
-            p.outlet[a * p.ny + y] = v;
+            p.outlet[a * p.ny + y] = v * (1.0f / Raw<T>::kScale);
         }
     }
     // Force density on this lane's nodes: node-centric spread (Eq. 15) of the
@@ -133,7 +133,7 @@ __device__ __forceinline__ void collide_store(float (&f)[9][NPL], T* __restrict_
         float d[9];
 #pragma unroll
         for (int a = 0; a < 9; a++) d[a] = f[a][i];
-        const Moments m = moments(d, p.urx, p.ury);
+        const Moments m = moments(d, p.urx, p.ury, 1.0f / Raw<T>::kScale);
         float a0 = m.dux, b0 = m.duy;
         uF[i] = 0.0f;
         if (forced) {
@@ -166,12 +166,12 @@ __device__ __forceinline__ void collide_store(float (&f)[9][NPL], T* __restrict_
             float o[NPL];
 #pragma unroll
             for (int i = 0; i < NPL; i++) {
-                const float ed = ex(a) * du[i] + ey(a) * dv[i];
+                const float ed = edot(a, du[i], dv[i]);
                 const float pdiff = __fmaf_rn(ed, __fmaf_rn(4.5f, ed, p.c1[a]), -pd0[i]);
                 const float deqw = __fmaf_rn(rho[i], pdiff, __fmul_rn(p.kr[a], drho[i]));
                 o[i] = __fmaf_rn(p.wom[a], deqw, __fmul_rn(p.one_m_omega, f[a][i]));
             }
-            if (store) Io<T>::template stv<NPL>(out + p.poff[a], o);
+            if (store) Raw<T>::template stv<NPL>(out + p.poff[a], o);
         }
     } else {
 #pragma unroll
@@ -179,16 +179,16 @@ __device__ __forceinline__ void collide_store(float (&f)[9][NPL], T* __restrict_
             float o[NPL];
 #pragma unroll
             for (int i = 0; i < NPL; i++) {
-                const float ed = ex(a) * du[i] + ey(a) * dv[i];
+                const float ed = edot(a, du[i], dv[i]);
                 const float pdiff = __fmaf_rn(ed, __fmaf_rn(4.5f, ed, p.c1[a]), -pd0[i]);
                 const float deqw = __fmaf_rn(rho[i], pdiff, __fmul_rn(p.kr[a], drho[i]));
                 float r = __fmaf_rn(p.wom[a], deqw, __fmul_rn(p.one_m_omega, f[a][i]));
-                const float eF = ex(a) * Fx[i] + ey(a) * Fy[i];
+                const float eF = edot(a, Fx[i], Fy[i]);
                 const float eu = p.eur[a] + ed;
                 const float g = __fmaf_rn(eF, __fmaf_rn(9.0f, eu, 3.0f), __fmul_rn(-3.0f, uF[i]));
                 o[i] = __fmaf_rn(p.wg[a], g, r);
             }
-            if (store) Io<T>::template stv<NPL>(out + p.poff[a], o);
+            if (store) Raw<T>::template stv<NPL>(out + p.poff[a], o);
         }
     }
 }
@@ -218,10 +218,10 @@ __device__ __forceinline__ void lbm_segment(const T* __restrict__ gin, T* __rest
         for (int a = 0; a < 9; a++) {
             const int dx = kPull ? -ex(a) : 0, dy = kPull ? -ey(a) : 0;
             const unsigned off = p.poff[a] + rowc + (unsigned)(dy * (int)p.rs);
-            Io<T>::template ldv<NPL>(gin + off, f[a]);
+            Raw<T>::template ldv<NPL>(gin + off, f[a]);
             float edge = 0.0f;
-            if (dx < 0 && lane0 && x0 > 0) edge = Io<T>::ld1(gin + (off - 1));
-            if (dx > 0 && lane31 && x0 + NPL < p.nxp) edge = Io<T>::ld1(gin + (off + NPL));
+            if (dx < 0 && lane0 && x0 > 0) edge = Raw<T>::ld1(gin + (off - 1));
+            if (dx > 0 && lane31 && x0 + NPL < p.nxp) edge = Raw<T>::ld1(gin + (off + NPL));
             if (dx < 0) {
                 float prev = __shfl_up_sync(kFull, f[a][NPL - 1], 1);
                 if (lane0) prev = edge;
@@ -257,14 +257,14 @@ __device__ __forceinline__ void lbm_segment(const T* __restrict__ gin, T* __rest
         }
         shift[a] = dx;
         if (live) {
-            Io<T>::template ldv<NPL>(gin + off, f[a]);
+            Raw<T>::template ldv<NPL>(gin + off, f[a]);
         } else {
 #pragma unroll
             for (int i = 0; i < NPL; i++) f[a][i] = 0.0f;
         }
         edge[a] = 0.0f;
-        if (dx < 0 && lane0 && live && x0 > 0) edge[a] = Io<T>::ld1(gin + (off - 1));
-        if (dx > 0 && lane31 && live && x0 + NPL < p.nxp) edge[a] = Io<T>::ld1(gin + (off + NPL));
+        if (dx < 0 && lane0 && live && x0 > 0) edge[a] = Raw<T>::ld1(gin + (off - 1));
+        if (dx > 0 && lane31 && live && x0 + NPL < p.nxp) edge[a] = Raw<T>::ld1(gin + (off + NPL));
     }
 #pragma unroll
     for (int a = 0; a < 9; a++) {
@@ -289,7 +289,7 @@ __device__ __forceinline__ void lbm_segment(const T* __restrict__ gin, T* __rest
         for (int a = 0; a < 9; a++) {
             const int sy = y - ey(a);
             if (sy < 0 || sy >= p.ny) {
-                const float add = -6.0f * wt(a) * p.eur[a];
+                const float add = -6.0f * wt(a) * p.eur[a] * Raw<T>::kScale;
 #pragma unroll
                 for (int i = 0; i < NPL; i++) f[a][i] += add;
             }
@@ -306,7 +306,7 @@ __device__ __forceinline__ void lbm_segment(const T* __restrict__ gin, T* __rest
                     float fe[9];
                     pull_box_node<T>(gin, p, x, y, fe);
 #pragma unroll
-                    for (int a = 0; a < 9; a++) f[a][i] = fe[a];
+                    for (int a = 0; a < 9; a++) f[a][i] = fe[a] * Raw<T>::kScale;
                 }
             }
         }
@@ -318,7 +318,7 @@ __device__ __forceinline__ void lbm_segment(const T* __restrict__ gin, T* __rest
                 float fe[9];
                 pull_node<T>(gin, p, x, y, fe);
 #pragma unroll
-                for (int a = 0; a < 9; a++) f[a][i] = fe[a];
+                for (int a = 0; a < 9; a++) f[a][i] = fe[a] * Raw<T>::kScale;
             }
         }
     }
@@ -336,19 +336,19 @@ collide_stream_kernel(const T* __restrict__ gin, T* __restrict__ gout, LatticePa
     constexpr int SW = 32 * NPL;
     const int lane = threadIdx.x & 31;
     const int nsegw = (p.nxp + SW - 1) / SW;
-    const int nw = gridDim.x * (blockDim.x >> 5);
     const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int y0 = w0 / nsegw, s0 = w0 - y0 * nsegw;
-    const int dy = nw / nsegw, ds = nw - dy * nsegw;
+    const int y0 = (int)((__umulhi((unsigned)w0, p.wmul) + (unsigned)w0) >> p.wshift);
+    const int s0 = w0 - y0 * nsegw;
     // Band segments wait for the IB kernel's forces inside lbm_segment; the
     // body-force reduction comes after block 0's lattice work, when the IB
     // kernel has long finished.
     // L2 prefetch of the segment a later wave of warps will process: its
     // loads then hit L2 instead of waiting on DRAM (one instruction per warp).
     if (p.pf_ahead > 0) {
-        const long long u2 = (long long)w0 + p.pf_ahead;
-        if (u2 < (long long)p.ny * nsegw) {
-            const int y2 = (int)(u2 / nsegw), x2 = (int)(u2 - (long long)y2 * nsegw) * SW;
+        const int u2 = w0 + p.pf_ahead;
+        if (u2 < (int)p.nwork) {
+            const int y2 = (int)((__umulhi((unsigned)u2, p.wmul) + (unsigned)u2) >> p.wshift);
+            const int x2 = (u2 - y2 * nsegw) * SW;
             constexpr int LE = 128 / (int)sizeof(T);            // elements per 128-byte line
             constexpr int LINES = (SW + LE - 1) / LE;
             for (int k = lane; k < 9 * LINES; k += 32) {
@@ -364,8 +364,8 @@ collide_stream_kernel(const T* __restrict__ gin, T* __restrict__ gout, LatticePa
     while (y < p.ny) {
         const int seg = band_segment(p, y, s * SW);
         lbm_segment<T, kPull, NPL>(gin, gout, p, y, s * SW, lane, seg);
-        s += ds;
-        y += dy;
+        s += p.wds;
+        y += p.wdy;
         if (s >= nsegw) {
             s -= nsegw;
             y += 1;
@@ -394,10 +394,10 @@ __device__ __forceinline__ void issue_interior(const T* __restrict__ gin, const 
     for (int a = 0; a < 9; a++) {
         const int dx = -ex(a), dy = -ey(a);
         const unsigned off = p.poff[a] + rowc + (unsigned)(dy * (int)p.rs);
-        Io<T>::template ldv<NPL>(gin + off, r.v[a]);
+        Raw<T>::template ldv<NPL>(gin + off, r.v[a]);
         r.e[a] = 0.0f;
-        if (dx < 0 && lane == 0 && x0 > 0) r.e[a] = Io<T>::ld1(gin + (off - 1));
-        if (dx > 0 && lane == 31 && x0 + NPL < p.nxp) r.e[a] = Io<T>::ld1(gin + (off + NPL));
+        if (dx < 0 && lane == 0 && x0 > 0) r.e[a] = Raw<T>::ld1(gin + (off - 1));
+        if (dx > 0 && lane == 31 && x0 + NPL < p.nxp) r.e[a] = Raw<T>::ld1(gin + (off + NPL));
     }
 }
 
@@ -464,7 +464,7 @@ collide_stream_pf_kernel(const T* __restrict__ gin, T* __restrict__ gout, Lattic
                         float fe[9];
                         pull_node<T>(gin, p, x, y, fe);
 #pragma unroll
-                        for (int a = 0; a < 9; a++) f[a][i] = fe[a];
+                        for (int a = 0; a < 9; a++) f[a][i] = fe[a] * Raw<T>::kScale;
                     }
                 }
             }
@@ -610,14 +610,14 @@ collide_stream_tma_kernel(const __grid_constant__ CUtensorMap tmap, const T* __r
                 for (int a = 0; a < 9; a++) {
                     const int dx = -ex(a);
                     const T* srow = tile + (a * C::BY + warp + 1 - ey(a)) * C::BX + C::H;
-                    Io<T>::template ldv<4>(srow + 4 * lane, f[a]);
+                    Raw<T>::template ldv<4>(srow + 4 * lane, f[a]);
                     if (dx < 0) {
                         float prev = __shfl_up_sync(kFull, f[a][3], 1);
-                        if (lane == 0) prev = Io<T>::ld1s(srow - 1);
+                        if (lane == 0) prev = Raw<T>::ld1s(srow - 1);
                         f[a][3] = f[a][2]; f[a][2] = f[a][1]; f[a][1] = f[a][0]; f[a][0] = prev;
                     } else if (dx > 0) {
                         float next = __shfl_down_sync(kFull, f[a][0], 1);
-                        if (lane == 31) next = Io<T>::ld1s(srow + C::TW);
+                        if (lane == 31) next = Raw<T>::ld1s(srow + C::TW);
                         f[a][0] = f[a][1]; f[a][1] = f[a][2]; f[a][2] = f[a][3]; f[a][3] = next;
                     }
                 }
@@ -633,27 +633,27 @@ collide_stream_tma_kernel(const __grid_constant__ CUtensorMap tmap, const T* __r
                 float v[4];
                 if (r >= 0 && r < C::BY) {                  // from shared memory
                     const T* srow = tile + (pa * C::BY + r) * C::BX + C::H;
-                    Io<T>::template ldv<4>(srow + 4 * lane, v);   // same bank group per lane
+                    Raw<T>::template ldv<4>(srow + 4 * lane, v);   // same bank group per lane
                     if (dx < 0) {
                         float prev = __shfl_up_sync(kFull, v[3], 1);
-                        if (lane == 0) prev = Io<T>::ld1s(srow - 1);
+                        if (lane == 0) prev = Raw<T>::ld1s(srow - 1);
                         v[3] = v[2]; v[2] = v[1]; v[1] = v[0]; v[0] = prev;
                     } else if (dx > 0) {
                         float next = __shfl_down_sync(kFull, v[0], 1);
-                        if (lane == 31) next = Io<T>::ld1s(srow + C::TW);
+                        if (lane == 31) next = Raw<T>::ld1s(srow + C::TW);
                         v[0] = v[1]; v[1] = v[2]; v[2] = v[3]; v[3] = next;
                     }
                 } else {                                    // periodic wrap row: global
                     const T* grow = gin + p.poff[pa] + (unsigned)sy * p.rs;
-                    if (live) Io<T>::template ldv<4>(grow + x0, v);
+                    if (live) Raw<T>::template ldv<4>(grow + x0, v);
                     else v[0] = v[1] = v[2] = v[3] = 0.0f;
                     if (dx < 0) {
                         float prev = __shfl_up_sync(kFull, v[3], 1);
-                        if (lane == 0) prev = (live && x0 > 0) ? Io<T>::ld1(grow + x0 - 1) : 0.0f;
+                        if (lane == 0) prev = (live && x0 > 0) ? Raw<T>::ld1(grow + x0 - 1) : 0.0f;
                         v[3] = v[2]; v[2] = v[1]; v[1] = v[0]; v[0] = prev;
                     } else if (dx > 0) {
                         float next = __shfl_down_sync(kFull, v[0], 1);
-                        if (lane == 31) next = (live && x0 + 4 < p.nxp) ? Io<T>::ld1(grow + x0 + 4) : 0.0f;
+                        if (lane == 31) next = (live && x0 + 4 < p.nxp) ? Raw<T>::ld1(grow + x0 + 4) : 0.0f;
                         v[0] = v[1]; v[1] = v[2]; v[2] = v[3]; v[3] = next;
                     }
                 }
@@ -666,7 +666,7 @@ collide_stream_tma_kernel(const __grid_constant__ CUtensorMap tmap, const T* __r
                 for (int a = 0; a < 9; a++) {
                     const int sy = y - ey(a);
                     if (sy < 0 || sy >= p.ny) {
-                        const float add = -6.0f * wt(a) * p.eur[a];
+                        const float add = -6.0f * wt(a) * p.eur[a] * Raw<T>::kScale;
 #pragma unroll
                         for (int i = 0; i < 4; i++) f[a][i] += add;
                     }
@@ -680,7 +680,7 @@ collide_stream_tma_kernel(const __grid_constant__ CUtensorMap tmap, const T* __r
                         float fe[9];
                         pull_node<T>(gin, p, x, y, fe);
 #pragma unroll
-                        for (int a = 0; a < 9; a++) f[a][i] = fe[a];
+                        for (int a = 0; a < 9; a++) f[a][i] = fe[a] * Raw<T>::kScale;
                     }
                 }
             }
@@ -917,6 +917,20 @@ __global__ void read_field_kernel(const T* __restrict__ g, LatticeParams p, int 
     else dst[n] = p.ury + m.duy;
 }
 
+// Division of the warp index by nsegw as a multiply and a shift (Granlund
+// and Montgomery, "Division by invariant integers using multiplication",
+// 1994): with s = ceil(log2 d) and m = floor(2^32 (2^s - d) / d) + 1,
+// n / d = (umulhi(n, m) + n) >> s for every n < 2^31.
+inline void set_warp_map(LatticeParams& p, int nsegw, long long nw) {
+    const unsigned long long d = (unsigned long long)nsegw;
+    int s = 0;
+    while ((1ull << s) < d) s++;
+    p.wmul = (unsigned)((((1ull << s) - d) << 32) / d + 1ull);
+    p.wshift = s;
+    p.wdy = (int)(nw / nsegw);
+    p.wds = (int)(nw - (long long)p.wdy * nsegw);
+}
+
 inline unsigned blocks_for(long long threads) {
     return (unsigned)((threads + kThreads - 1) / kThreads);
 }
@@ -925,12 +939,15 @@ template <typename T, int NPL, int MB>
 cudaError_t collide_stream_tn(bool pull, const void* gin, void* gout, LatticeParams p, int grid,
                               bool pdl, cudaStream_t st) {
     constexpr int SW = 32 * NPL;
-    p.nwork = (long long)p.ny * ((p.nxp + SW - 1) / SW);
+    const int nsegw = (p.nxp + SW - 1) / SW;
+    p.nwork = (long long)p.ny * nsegw;
     const long long need = (p.nwork * 32 + kThreads - 1) / kThreads;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)std::min<long long>(need, (long long)grid));
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = 0;
+    const long long nw = (long long)cfg.gridDim.x * (kThreads / 32);
+    set_warp_map(p, nsegw, nw);
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
