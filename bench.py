@@ -402,7 +402,7 @@ def our_arm(args):
     # ---- kernel variant: the library's autotuner times each candidate on
     # this lattice (L2 evicted before every step, median of 32 steps) ----
     names = {1: "reg4", 2: "reg2", 3: "tma8x2", 4: "tma8x3", 5: "tma16x2", 6: "reg4pf", 7: "reg2pf",
-             8: "reg1", 9: "reg2o", 10: "reg2o_l2pf"}
+             8: "reg1", 9: "reg2o", 10: "reg2o_l2pf", 11: "reg4_l2pf"}
     if args.variant == 0:
         best, tms = lat.autotune(32, True)
         tune = {names[v]: t for v, t in tms.items()}
@@ -545,7 +545,7 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=90.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="bench", choices=["bench", "kernel", "batch", "adjoint"])
-    ap.add_argument("--variant", type=int, default=0, choices=list(range(11)))
+    ap.add_argument("--variant", type=int, default=0, choices=list(range(12)))
     ap.add_argument("--layout", default="rows", choices=["rows", "planes"])
     args = ap.parse_args()
     if args.warmup < 3:

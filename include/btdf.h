@@ -242,6 +242,10 @@ int btdf_profile_enable(btdf_ctx *ctx, int32_t on);
 int btdf_profile_read(btdf_ctx *ctx, double *ms_ib, double *ms_lbm, int64_t *launches_ib,
                       int64_t *launches_lbm);
 
+/* Number of collide-stream variants, 0 (automatic) included: the length of
+ * btdf_autotune's ms output. */
+#define BTDF_VARIANT_COUNT 12
+
 /* Variant of the fused collide-stream kernel.  Results do not depend on it.
  *   0 automatic (2 for FP32 storage, 1 for FP16 / BF16)
  *   1 register-pipelined warps, 4 nodes per lane (16-byte FP32 vectors)
@@ -255,8 +259,9 @@ int btdf_profile_read(btdf_ctx *ctx, double *ms_ib, double *ms_lbm, int64_t *lau
  *   9 register warps, 2 nodes per lane, 5 resident blocks per SM
  *  10 as 9, and each warp prefetches into L2 the row segment that a warp
  *     half a wave later will process
+ *  11 as 1, with the L2 prefetch of 10
  * grid_blocks caps the grid (0 = default: one 32 x NPL-node row segment per
- * warp for variants 1, 2, 8, 9 and 10, so the block scheduler balances the SMs;
+ * warp for variants 1, 2 and 8-11, so the block scheduler balances the SMs;
  * SM count x resident blocks per SM for the persistent variants 3-7).
  * Synchronizes and drops cached CUDA graphs.
  * Errors: EINVAL (unknown variant, TMA variant without tensor maps). */
@@ -266,7 +271,7 @@ int btdf_tune(btdf_ctx *ctx, int32_t variant, int32_t grid_blocks);
 int btdf_device_bytes(const btdf_ctx *ctx, size_t *bytes);
 
 /* Autotuner of the collide-stream launch: times every available variant of
- * btdf_tune (1..10; the TMA variants only where tensor maps were encoded) on
+ * btdf_tune (1..BTDF_VARIANT_COUNT-1; the TMA variants only where tensor maps were encoded) on
  * this context's own lattice, `steps` steps each after 3 untimed ones, every
  * step (IB and LBM stage, overlapped as in btdf_step) between CUDA events on
  * the context stream, with the L2 cache evicted before each step when
@@ -274,7 +279,7 @@ int btdf_device_bytes(const btdf_ctx *ctx, size_t *bytes);
  * populations, the step counter, the force history and the last step's
  * marker results are restored afterwards, so the simulation does not
  * advance.  Outputs (may be NULL): *chosen, and ms[v] = median ms per step of
- * variant v for v = 0..10 (-1 where not timed).  Needs temporary device memory
+ * variant v for v = 0..BTDF_VARIANT_COUNT-1 (-1 where not timed).  Needs temporary device memory
  * for one copy of the populations and, with flush_l2, four times the L2 size.
  * Synchronizes.  Errors: EINVAL (steps outside 1..100000), ESTATE (no fields),
  * ENOMEM / ECUDA. */

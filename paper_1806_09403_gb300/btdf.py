@@ -41,7 +41,7 @@ EXPORTS = [
     "btdf_read_forces_async", "btdf_add_cylinder", "btdf_set_boundary_velocity",
 ]
 STATIC_MAX_MARKERS = 2048
-VARIANT_COUNT = 11          # collide-stream variants 0 (automatic) .. 10, see btdf_tune
+VARIANT_COUNT = 12          # BTDF_VARIANT_COUNT: variants 0 (automatic) .. 11, see btdf_tune
 STATE_HEADER_BYTES = 40
 
 

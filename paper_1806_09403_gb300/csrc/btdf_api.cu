@@ -17,6 +17,8 @@
 #include <string>
 #include <vector>
 
+static_assert(btdf::kVarCount == BTDF_VARIANT_COUNT, "variant count of the C ABI");
+
 namespace btdf {
 namespace {
 
@@ -188,7 +190,7 @@ struct btdf_ctx {
 
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     long long pf_grid[2] = {1, 1};                 // software-pipelined kernel [npl 4/2]
-    long long pf_units[2] = {0, 0};                // L2 prefetch distance of variant 10 [local/pull]
+    long long pf_units[2][2] = {};                 // L2 prefetch distance of variants 10, 11 [local/pull]
     long long tma_grid[kVarCount] = {};  // persistent grid of each TMA variant
     int variant = kVarAuto;              // LBM kernel variant (btdf_tune)
     int grid_override = 0;               // 0: SMs x resident blocks
@@ -421,7 +423,8 @@ int enqueue_step(btdf_ctx* ctx, cudaStream_t st, bool pull, int cur, bool prof) 
                          : pf                   ? (int)ctx->pf_grid[v == kVarReg2Pf ? 1 : 0]
                                                 : kFullGrid;
         LatticeParams q = p;
-        if (v == kVarReg2OccPf) q.pf_ahead = (int)ctx->pf_units[pull ? 1 : 0];
+        if (v == kVarReg2OccPf || v == kVarReg4L2Pf)
+            q.pf_ahead = (int)ctx->pf_units[v == kVarReg4L2Pf ? 1 : 0][pull ? 1 : 0];
         CK(launch_collide_stream(ctx->cfg.storage, pull, v, ctx->g[cur], ctx->g[1 - cur], q, grid, pdl, st));
     }
     if (prof) CK(cudaEventRecord(e2, st));
@@ -872,9 +875,12 @@ int btdf_create(const btdf_config* cfg, void* stream, btdf_ctx** out) {
         ctx->pf_grid[1] = (long long)sms * collide_stream_blocks_per_sm(c.storage, true, kVarReg2Pf);
         // half a wave of resident warps (measured: 5% faster on 8192 x 4096,
         // no gain on 1600 x 800, where the autotuner keeps variant 9)
-        for (int pull = 0; pull < 2; pull++)
-            ctx->pf_units[pull] =
-                (long long)sms * collide_stream_blocks_per_sm(c.storage, pull != 0, kVarReg2OccPf) * (kThreads / 32) / 2;
+        for (int k = 0; k < 2; k++)
+            for (int pull = 0; pull < 2; pull++)
+                ctx->pf_units[k][pull] =
+                    (long long)sms *
+                    collide_stream_blocks_per_sm(c.storage, pull != 0, k ? kVarReg4L2Pf : kVarReg2OccPf) *
+                    (kThreads / 32) / 2;
     }
     const size_t bytes = (size_t)9 * ctx->plane * ctx->elem;
     for (int i = 0; i < 2; i++) {

@@ -196,7 +196,8 @@ enum : int {
     kVarReg1 = 8,      // 1 node per lane, 6 blocks per SM (<= 40 registers)
     kVarReg2Occ = 9,   // 2 nodes per lane, 5 blocks per SM (<= 48 registers)
     kVarReg2OccPf = 10, // as 9, each warp also prefetches a later row segment into L2
-    kVarCount = 11
+    kVarReg4L2Pf = 11, // as 1, with the L2 prefetch of 10
+    kVarCount = 12
 };
 // map: 3-D tensor map (x, y, population) of the input buffer with box
 // (128 + 2 * tma_halo(storage), tma_box_rows(variant), 9).

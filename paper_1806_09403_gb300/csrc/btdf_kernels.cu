@@ -1002,6 +1002,7 @@ cudaError_t collide_stream_t(bool pull, int variant, const void* gin, void* gout
     case kVarReg1: return collide_stream_tn<T, 1, 6>(pull, gin, gout, p, grid, pdl, st);
     case kVarReg2Occ:
     case kVarReg2OccPf: return collide_stream_tn<T, 2, 5>(pull, gin, gout, p, grid, pdl, st);
+    case kVarReg4L2Pf: return collide_stream_tn<T, 4, 3>(pull, gin, gout, p, grid, pdl, st);
     default: return collide_stream_tn<T, 4, 3>(pull, gin, gout, p, grid, pdl, st);
     }
 }
@@ -1027,6 +1028,7 @@ int blocks_per_sm_t(bool pull, int variant) {
     case kVarReg1: return blocks_per_sm_tn<T, 1, 6>(pull);
     case kVarReg2Occ:
     case kVarReg2OccPf: return blocks_per_sm_tn<T, 2, 5>(pull);
+    case kVarReg4L2Pf: return blocks_per_sm_tn<T, 4, 3>(pull);
     default: return blocks_per_sm_tn<T, 4, 3>(pull);
     }
 }

@@ -37,6 +37,16 @@ def test_config_struct_size_matches():
     assert ctypes.sizeof(B.btdf_config) == 72
 
 
+def test_variant_count_matches_header():
+    src = open(os.path.join(ROOT, "include", "btdf.h")).read()
+    m = re.search(r"#define BTDF_VARIANT_COUNT (\d+)", src)
+    assert m and int(m.group(1)) == B.VARIANT_COUNT
+    # every variant the header documents under btdf_tune, 0 .. count - 1
+    doc = src[src.index("Variant of the fused collide-stream kernel"):src.index("int btdf_tune(")]
+    listed = sorted({int(v) for v in re.findall(r"\n \*\s+(\d+) ", doc)})
+    assert listed == list(range(B.VARIANT_COUNT))
+
+
 def test_version_and_status_strings():
     assert B.btdf_version() >= 1
     for rc in (0, -1, -2, -3, -4, -5, -6):

@@ -263,8 +263,8 @@ def test_graph_replay_matches_direct_launches():
     assert np.array_equal(a.forces(0)[0], b.forces(0)[0])
 
 
-VARIANTS = [(1, 0), (2, 0), (3, 0), (4, 0), (5, 0), (6, 0), (7, 0), (8, 0), (9, 0), (10, 0), (1, 7),
-            (2, 1), (3, 5), (5, 1), (6, 3), (7, 1), (8, 5), (9, 2), (10, 3)]
+VARIANTS = [(1, 0), (2, 0), (3, 0), (4, 0), (5, 0), (6, 0), (7, 0), (8, 0), (9, 0), (10, 0), (11, 0),
+            (1, 7), (2, 1), (3, 5), (5, 1), (6, 3), (7, 1), (8, 5), (9, 2), (10, 3), (11, 4)]
 
 
 @pytest.mark.parametrize("storage", [B.BTDF_F32, B.BTDF_F16DEV, B.BTDF_BF16DEV])
@@ -433,7 +433,7 @@ def test_convective_outlet_1000_steps():
     b.step(300)
     assert np.array_equal(a.field(B.FIELD_UX), b.field(B.FIELD_UX))
     outs = []
-    for variant in (1, 2, 3, 9, 10):
+    for variant in (1, 2, 3, 9, 10, 11):
         c = B.Lattice.from_case(case)
         c.tune(variant, 0)
         c.step(120)
