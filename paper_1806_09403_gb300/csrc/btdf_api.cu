@@ -337,6 +337,12 @@ LatticeParams lattice_params(const btdf_ctx* ctx) {
             p.wom[a] = (float)(w / tau * store_scale(ctx->cfg.storage));
             p.wg[a] = (float)(w * (1.0 - 0.5 / tau) * store_scale(ctx->cfg.storage));
         }
+        for (int a = 0; a < 9; a++) {
+            p.c1p[a] = make_float2(p.c1[a], p.c1[a]);
+            p.krp[a] = make_float2(p.kr[a], p.kr[a]);
+            p.womp[a] = make_float2(p.wom[a], p.wom[a]);
+        }
+        p.omop = make_float2(p.one_m_omega, p.one_m_omega);
     }
     p.nwork = (long long)ctx->cfg.ny * ctx->nseg;
     // planar: [9][ny][nxp]; row-interleaved: [ny][9][nxp]

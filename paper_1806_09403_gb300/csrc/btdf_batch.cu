@@ -147,6 +147,12 @@ LatticeParams base_params(const btdf_batch* bt, int c) {
         p.wom[a] = (float)(w / k.tau * store_scale(bt->storage));
         p.wg[a] = (float)(w * (1.0 - 0.5 / k.tau) * store_scale(bt->storage));
     }
+    for (int a = 0; a < 9; a++) {
+        p.c1p[a] = make_float2(p.c1[a], p.c1[a]);
+        p.krp[a] = make_float2(p.kr[a], p.kr[a]);
+        p.womp[a] = make_float2(p.wom[a], p.wom[a]);
+    }
+    p.omop = make_float2(p.one_m_omega, p.one_m_omega);
     p.gx = (float)k.gx;
     p.gy = (float)k.gy;
     p.nwork = (long long)k.ny * bt->nseg[c];

@@ -212,6 +212,45 @@ __device__ __forceinline__ Moments moments(const float d[9], float urx, float ur
     return m;
 }
 
+// ---- packed FP32x2 arithmetic (two nodes per instruction) -------------------
+
+// One instruction, two IEEE round-to-nearest operations: the same values as
+// the scalar __fadd_rn / __fmul_rn / __fmaf_rn on each half.
+__device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.0f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// moments() for two nodes at once, operation for operation.
+struct Moments2 {
+    float2 drho, rho, inv, dux, duy;
+};
+__device__ __forceinline__ Moments2 moments2(const float2 d[9], float urx, float ury, float s = 1.0f) {
+    Moments2 m;
+    float2 r = add2(add2(add2(d[0], d[1]), add2(d[2], d[3])), add2(add2(d[4], d[5]), add2(d[6], d[7])));
+    r = add2(r, d[8]);
+    float2 jx = add2(add2(sub2(d[1], d[3]), sub2(d[5], d[6])), sub2(d[8], d[7]));
+    float2 jy = sub2(add2(sub2(d[2], d[4]), add2(d[5], d[6])), add2(d[7], d[8]));
+    if (s != 1.0f) {
+        r = mul2(r, f2(s));
+        jx = mul2(jx, f2(s));
+        jy = mul2(jy, f2(s));
+    }
+    m.drho = r;
+    m.rho = add2(f2(1.0f), r);
+    m.inv = make_float2(__fdividef(1.0f, m.rho.x), __fdividef(1.0f, m.rho.y));
+    m.dux = mul2(fma2(m.drho, f2(-urx), jx), m.inv);
+    m.duy = mul2(fma2(m.drho, f2(-ury), jy), m.inv);
+    return m;
+}
+
+// edot() for two nodes; nx, ny are -x, -y.
+__device__ __forceinline__ float2 edot2(int a, float2 x, float2 y, float2 nx, float2 ny) {
+    const float2 sx = ex(a) > 0 ? x : nx, sy = ey(a) > 0 ? y : ny;
+    return ex(a) == 0 ? (ey(a) == 0 ? f2(0.0f) : sy) : (ey(a) == 0 ? sx : add2(sx, sy));
+}
+
 // ---- pulls with boundary rules ---------------------------------------------
 
 // Source of population a at node (x, y) under the rules of the y boundaries:

@@ -116,6 +116,10 @@ struct LatticeParams {
     // wom and wg times the storage scale (2^10 for FP16, else 1): the LBM
     // kernels collide the populations at their stored scale.
     float eur[9], c1[9], kr[9], wom[9], wg[9];
+    // The same constants duplicated into pairs for the packed FP32x2
+    // arithmetic of two nodes at once (c1, kr, wom), and 1 - 1/tau.
+    float2 c1p[9], krp[9], womp[9];
+    float2 omop;
     float gx, gy;              // uniform body force
     // Convective outlet (null: zero-gradient): the outlet column's
     // post-streaming deviations of the previous step, [9][ny], and the

@@ -127,29 +127,48 @@ __device__ __forceinline__ void collide_store(float (&f)[9][NPL], T* __restrict_
 
     // Moments (Eqs. 9-10) and the velocity correction u = u* + f / (2 rho)
     // (Eq. 11), as deviations from the reference state.
-    float drho[NPL], rho[NPL], du[NPL], dv[NPL], pd0[NPL], uF[NPL];
+    float drho[NPL], rho[NPL], du[NPL], dv[NPL], pd0[NPL], uF[NPL], inv[NPL];
+    if constexpr (NPL % 2 == 0) {
+        // node pairs through the packed FP32x2 instructions
+#pragma unroll
+        for (int j = 0; j < NPL; j += 2) {
+            float2 d[9];
+#pragma unroll
+            for (int a = 0; a < 9; a++) d[a] = make_float2(f[a][j], f[a][j + 1]);
+            const Moments2 m = moments2(d, p.urx, p.ury, 1.0f / Raw<T>::kScale);
+            drho[j] = m.drho.x; drho[j + 1] = m.drho.y;
+            rho[j] = m.rho.x; rho[j + 1] = m.rho.y;
+            inv[j] = m.inv.x; inv[j + 1] = m.inv.y;
+            du[j] = m.dux.x; du[j + 1] = m.dux.y;
+            dv[j] = m.duy.x; dv[j + 1] = m.duy.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < NPL; i++) {
+            float d[9];
+#pragma unroll
+            for (int a = 0; a < 9; a++) d[a] = f[a][i];
+            const Moments m = moments(d, p.urx, p.ury, 1.0f / Raw<T>::kScale);
+            drho[i] = m.drho;
+            rho[i] = m.rho;
+            inv[i] = m.inv;
+            du[i] = m.dux;
+            dv[i] = m.duy;
+        }
+    }
 #pragma unroll
     for (int i = 0; i < NPL; i++) {
-        float d[9];
-#pragma unroll
-        for (int a = 0; a < 9; a++) d[a] = f[a][i];
-        const Moments m = moments(d, p.urx, p.ury, 1.0f / Raw<T>::kScale);
-        float a0 = m.dux, b0 = m.duy;
         uF[i] = 0.0f;
         if (forced) {
             Fx[i] += p.gx;
             Fy[i] += p.gy;
-            a0 = __fmaf_rn(__fmul_rn(0.5f, Fx[i]), m.inv, a0);
-            b0 = __fmaf_rn(__fmul_rn(0.5f, Fy[i]), m.inv, b0);
-            uF[i] = __fmaf_rn(p.urx + a0, Fx[i], __fmul_rn(p.ury + b0, Fy[i]));
+            du[i] = __fmaf_rn(__fmul_rn(0.5f, Fx[i]), inv[i], du[i]);
+            dv[i] = __fmaf_rn(__fmul_rn(0.5f, Fy[i]), inv[i], dv[i]);
+            uF[i] = __fmaf_rn(p.urx + du[i], Fx[i], __fmul_rn(p.ury + dv[i], Fy[i]));
         }
-        drho[i] = m.drho;
-        rho[i] = m.rho;
-        du[i] = a0;
-        dv[i] = b0;
-        float t = __fmaf_rn(a0, a0, __fmul_rn(b0, b0));
-        t = __fmaf_rn(2.0f * p.urx, a0, t);
-        t = __fmaf_rn(2.0f * p.ury, b0, t);
+        float t = __fmaf_rn(du[i], du[i], __fmul_rn(dv[i], dv[i]));
+        t = __fmaf_rn(2.0f * p.urx, du[i], t);
+        t = __fmaf_rn(2.0f * p.ury, dv[i], t);
         pd0[i] = __fmul_rn(1.5f, t);
     }
 
@@ -160,7 +179,34 @@ __device__ __forceinline__ void collide_store(float (&f)[9][NPL], T* __restrict_
     //        + (1 - 1/(2 tau)) w [e.F (3 + 9 e.u) - 3 u.F]
     T* const out = gout + rowoff;
     const bool store = live && x0 < p.nx;
-    if (!forced) {
+    if (NPL % 2 == 0 && !forced) {
+        constexpr int NP = NPL / 2 > 0 ? NPL / 2 : 1;
+        float2 U[NP], V[NP], nU[NP], nV[NP], D[NP], R[NP], P[NP];
+#pragma unroll
+        for (int j = 0; j < NP; j++) {
+            U[j] = make_float2(du[2 * j], du[2 * j + 1]);
+            V[j] = make_float2(dv[2 * j], dv[2 * j + 1]);
+            nU[j] = mul2(U[j], f2(-1.0f));
+            nV[j] = mul2(V[j], f2(-1.0f));
+            D[j] = make_float2(drho[2 * j], drho[2 * j + 1]);
+            R[j] = make_float2(rho[2 * j], rho[2 * j + 1]);
+            P[j] = make_float2(-pd0[2 * j], -pd0[2 * j + 1]);
+        }
+#pragma unroll
+        for (int a = 0; a < 9; a++) {
+            float o[NPL];
+#pragma unroll
+            for (int j = 0; j < NP; j++) {
+                const float2 ed = edot2(a, U[j], V[j], nU[j], nV[j]);
+                const float2 pdiff = fma2(ed, fma2(f2(4.5f), ed, p.c1p[a]), P[j]);
+                const float2 deqw = fma2(R[j], pdiff, mul2(p.krp[a], D[j]));
+                const float2 r = fma2(p.womp[a], deqw, mul2(p.omop, make_float2(f[a][2 * j], f[a][2 * j + 1])));
+                o[2 * j] = r.x;
+                o[2 * j + 1] = r.y;
+            }
+            if (store) Raw<T>::template stv<NPL>(out + p.poff[a], o);
+        }
+    } else if (!forced) {
 #pragma unroll
         for (int a = 0; a < 9; a++) {
             float o[NPL];
