@@ -886,7 +886,7 @@ int btdf_create(const btdf_config* cfg, void* stream, btdf_ctx** out) {
                 ctx->pf_units[k][pull] =
                     (long long)sms *
                     collide_stream_blocks_per_sm(c.storage, pull != 0, k ? kVarReg4L2Pf : kVarReg2OccPf) *
-                    (kThreads / 32) / 2;
+                    (collide_stream_block_threads(c.storage, k ? kVarReg4L2Pf : kVarReg2OccPf) / 32) / 2;
     }
     const size_t bytes = (size_t)9 * ctx->plane * ctx->elem;
     for (int i = 0; i < 2; i++) {
