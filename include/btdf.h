@@ -261,7 +261,8 @@ int btdf_profile_read(btdf_ctx *ctx, double *ms_ib, double *ms_lbm, int64_t *lau
  *     half a wave later will process
  *  11 as 1, with the L2 prefetch of 10
  * grid_blocks caps the grid, counted in blocks of the variant: 256 threads,
- * or 128 for variants 1, 2 and 8-11 with FP16 / BF16 storage.  0 = default:
+ * or 128 for variant 2 and, with FP16 / BF16 storage, variants 1 and 8-11.
+ * 0 = default:
  * one 32 x NPL-node row segment per warp for variants 1, 2 and 8-11, so the
  * block scheduler balances the SMs; SM count x resident blocks per SM for
  * the persistent variants 3-7.

@@ -17,10 +17,15 @@ namespace btdf {
 constexpr int kSeg = 128;
 constexpr int kNodesPerLane = 4;
 constexpr int kThreads = 256;
-// Threads per block of the register LBM kernels: 128 with 16-bit storage
-// (measured 5% faster on 8192 x 4096 FP16, equal at 1600 x 800), 256 with
-// FP32 (the 128-thread form was 11% slower on 8192 x 4096).
-__host__ __device__ constexpr int lbm_block_threads(int elem_bytes) { return elem_bytes == 2 ? 128 : 256; }
+// Threads per block of the register LBM kernels (npl nodes per lane, minb
+// resident 256-thread blocks per SM): 128 with 16-bit storage (measured 5%
+// faster on 8192 x 4096 FP16, equal at 1600 x 800) and for the FP32 kernel of
+// 2 nodes per lane at 64 registers (2% faster at 1600 x 800); 256 for the
+// other FP32 kernels (the 128-thread form of the 5-block kernel was 11% slower
+// on 8192 x 4096).
+__host__ __device__ constexpr int lbm_block_threads(int elem_bytes, int npl, int minb) {
+    return (elem_bytes == 2 || (npl == 2 && minb == 4)) ? 128 : 256;
+}
 
 // D2Q9 velocities and weights (Eq. 8 and the weights stated below Eq. 7).
 __host__ __device__ constexpr int ex(int a) {

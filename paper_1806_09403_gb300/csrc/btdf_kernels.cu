@@ -377,7 +377,8 @@ __device__ __forceinline__ void lbm_segment(const T* __restrict__ gin, T* __rest
 // segment per warp, so the block scheduler balances the SMs; a capped grid
 // makes the kernel persistent.
 template <typename T, bool kPull, int NPL, int MINB>
-__global__ void __launch_bounds__(lbm_block_threads(sizeof(T)), MINB * kThreads / lbm_block_threads(sizeof(T)))
+__global__ void __launch_bounds__(lbm_block_threads(sizeof(T), NPL, MINB),
+                                  MINB * kThreads / lbm_block_threads(sizeof(T), NPL, MINB))
 collide_stream_kernel(const T* __restrict__ gin, T* __restrict__ gout, LatticeParams p) {
     constexpr int SW = 32 * NPL;
     const int lane = threadIdx.x & 31;
@@ -985,7 +986,7 @@ template <typename T, int NPL, int MB>
 cudaError_t collide_stream_tn(bool pull, const void* gin, void* gout, LatticeParams p, int grid,
                               bool pdl, cudaStream_t st) {
     constexpr int SW = 32 * NPL;
-    constexpr int BT = lbm_block_threads(sizeof(T));
+    constexpr int BT = lbm_block_threads(sizeof(T), NPL, MB);
     const int nsegw = (p.nxp + SW - 1) / SW;
     p.nwork = (long long)p.ny * nsegw;
     const long long need = (p.nwork * 32 + BT - 1) / BT;
@@ -1034,8 +1035,8 @@ int pf_blocks_tn() {
 
 // Register variants: nodes per lane and the resident blocks per SM the
 // register budget is cut for, counted in 256-thread blocks (3 x 256 threads
-// <= 80 registers, 4 <= 64, 5 <= 48, 6 <= 40); with 16-bit storage the
-// blocks have 128 threads and twice as many are resident.
+// <= 80 registers, 4 <= 64, 5 <= 48, 6 <= 40); where lbm_block_threads
+// picks 128-thread blocks, twice as many are resident.
 template <typename T>
 cudaError_t collide_stream_t(bool pull, int variant, const void* gin, void* gout, const LatticeParams& p,
                              int grid, bool pdl, cudaStream_t st) {
@@ -1060,10 +1061,10 @@ int blocks_per_sm_tn(bool pull) {
     int n = 0;
     if (pull)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, collide_stream_kernel<T, true, NPL, MB>,
-                                                      lbm_block_threads(sizeof(T)), 0);
+                                                      lbm_block_threads(sizeof(T), NPL, MB), 0);
     else
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, collide_stream_kernel<T, false, NPL, MB>,
-                                                      lbm_block_threads(sizeof(T)), 0);
+                                                      lbm_block_threads(sizeof(T), NPL, MB), 0);
     return n > 0 ? n : 1;
 }
 
@@ -1284,7 +1285,14 @@ int collide_stream_block_threads(int storage, int variant) {
     if (variant == kVarTma8x2 || variant == kVarTma8x3 || variant == kVarTma16x2)
         return -1;   // the TMA kernels size their own blocks
     if (variant == kVarReg4Pf || variant == kVarReg2Pf) return kThreads;
-    return lbm_block_threads(storage == kStoreF32 ? 4 : 2);
+    const int eb = storage == kStoreF32 ? 4 : 2;
+    switch (variant) {
+    case kVarReg2: return lbm_block_threads(eb, 2, 4);
+    case kVarReg1: return lbm_block_threads(eb, 1, 6);
+    case kVarReg2Occ:
+    case kVarReg2OccPf: return lbm_block_threads(eb, 2, 5);
+    default: return lbm_block_threads(eb, 4, 3);
+    }
 }
 
 int collide_stream_blocks_per_sm(int storage, bool pull, int variant) {
