@@ -166,11 +166,17 @@ __device__ __forceinline__ void collide_store(float (&f)[9][NPL], T* __restrict_
             dv[i] = __fmaf_rn(__fmul_rn(0.5f, Fy[i]), inv[i], dv[i]);
             uF[i] = __fmaf_rn(p.urx + du[i], Fx[i], __fmul_rn(p.ury + dv[i], Fy[i]));
         }
-        float t = __fmaf_rn(du[i], du[i], __fmul_rn(dv[i], dv[i]));
-        t = __fmaf_rn(2.0f * p.urx, du[i], t);
-        t = __fmaf_rn(2.0f * p.ury, dv[i], t);
-        pd0[i] = __fmul_rn(1.5f, t);
     }
+    // 1.5 (2 U_r.du + du^2), the velocity part shared by all populations
+    auto velocity_term = [&]() {
+#pragma unroll
+        for (int i = 0; i < NPL; i++) {
+            float t = __fmaf_rn(du[i], du[i], __fmul_rn(dv[i], dv[i]));
+            t = __fmaf_rn(2.0f * p.urx, du[i], t);
+            t = __fmaf_rn(2.0f * p.ury, dv[i], t);
+            pd0[i] = __fmul_rn(1.5f, t);
+        }
+    };
 
     // Collision (Eqs. 5-7), one population at a time, in the form
     //   d_eq / w = drho (1 + P(U_r)) + rho (P(u) - P(U_r))
@@ -190,7 +196,11 @@ __device__ __forceinline__ void collide_store(float (&f)[9][NPL], T* __restrict_
             nV[j] = mul2(V[j], f2(-1.0f));
             D[j] = make_float2(drho[2 * j], drho[2 * j + 1]);
             R[j] = make_float2(rho[2 * j], rho[2 * j + 1]);
-            P[j] = make_float2(-pd0[2 * j], -pd0[2 * j + 1]);
+            // -pd0 of velocity_term for the pair (-1.5 t is exactly -(1.5 t))
+            float2 t = fma2(U[j], U[j], mul2(V[j], V[j]));
+            t = fma2(f2(2.0f * p.urx), U[j], t);
+            t = fma2(f2(2.0f * p.ury), V[j], t);
+            P[j] = mul2(f2(-1.5f), t);
         }
 #pragma unroll
         for (int a = 0; a < 9; a++) {
@@ -207,6 +217,7 @@ __device__ __forceinline__ void collide_store(float (&f)[9][NPL], T* __restrict_
             if (store) Raw<T>::template stv<NPL>(out + p.poff[a], o);
         }
     } else if (!forced) {
+        velocity_term();
 #pragma unroll
         for (int a = 0; a < 9; a++) {
             float o[NPL];
@@ -220,6 +231,7 @@ __device__ __forceinline__ void collide_store(float (&f)[9][NPL], T* __restrict_
             if (store) Raw<T>::template stv<NPL>(out + p.poff[a], o);
         }
     } else {
+        velocity_term();
 #pragma unroll
         for (int a = 0; a < 9; a++) {
             float o[NPL];
