@@ -10,6 +10,9 @@
 * Implicit direct forcing (Eq. 17) and implicit velocity correction (Eq. A50)
   give the same force field (Appendix A).
 * BTDF reduces the boundary slip (Eq. 45) relative to DF (drs = dh), Sec. 5.2.
+* On a periodic flat wall with ds = dh and drs = 1 / sum(delta^2) one BTDF
+  pass makes the interpolated corrected velocity equal U_b exactly, which
+  fixes the factor 2 rho of Eq. 20 and the half step f / (2 rho) of Eq. 11.
 """
 import json
 import math
@@ -231,3 +234,59 @@ def test_taylor_green_with_circle_second_order():
         assert 1.7 < math.log2(a / b) < 2.4, e
         assert math.log2(ab / bb) > 1.7, e
 
+
+
+def _flat_wall(kind, yoff, rho0, ustar, ub, nf=1):
+    """A periodic line of markers at unit spacing along x over a uniform state
+    (rho0, ustar), thickness drs = 1 / sum_j delta(y_j - Y)^2; one step."""
+    nx, ny = 20, 12
+    Y0 = 5.0 + yoff
+    ssq = sum(O.delta(kind, j - Y0) ** 2 for j in range(ny))
+    drs = 1.0 / ssq
+    s = O.Sim(nx, ny, 0.8, 0.0, W.BCX_PERIODIC, W.BCY_PERIODIC, 0.0, 0.0, kind, nf)
+    z = np.zeros((ny, nx))
+    s.init_fields(z + rho0, z + ustar[0], z + ustar[1])
+    X = np.arange(nx) + 0.3
+    Y = np.full(nx, Y0)
+    s.add_body(X, Y, 1.0, np.full(nx, ub[0]), np.full(nx, ub[1]), drs=drs)
+    s.step(1)
+    return s, drs, Y0
+
+
+@pytest.mark.parametrize("kind", [2, 3, 4, 5])
+@pytest.mark.parametrize("yoff", [0.0, 0.2, 0.5])
+def test_flat_wall_single_pass_is_exact_no_slip(kind, yoff):
+    """Eqs. 11, 14, 15, 20 on a periodic flat wall with ds = dh.
+
+    With markers at unit spacing the x weights of every node sum to one over
+    the markers, so spreading a uniform force F gives f(y) = F drs delta(y - Y)
+    and the interpolation back gives D_I u = u* + F drs sum_j delta_j^2 / (2 rho).
+    With drs = 1 / sum_j delta_j^2 (the flat-wall thickness of Eq. 25) and
+    F = 2 rho (U_b - u*) (Eq. 20) this is U_b exactly, for any rho and u*.
+    A force rho (U_b - u*), a correction u* + f / rho, or rho0 = 1 in place of
+    the interpolated density all miss U_b by a fraction of U_b - u*."""
+    rho0, ustar, ub = 1.037, (0.031, -0.012), (0.004, 0.009)
+    s, drs, Y0 = _flat_wall(kind, yoff, rho0, ustar, ub)
+    d = s.marker_diag(0)
+    F = [2.0 * rho0 * (ub[0] - ustar[0]), 2.0 * rho0 * (ub[1] - ustar[1])]
+    assert np.abs(d["Usx"] - ustar[0]).max() < 1e-15 and np.abs(d["Usy"] - ustar[1]).max() < 1e-15
+    assert np.abs(d["rho"] - rho0).max() < 1e-14
+    assert np.abs(d["Fbx"] - F[0]).max() < 1e-14 and np.abs(d["Fby"] - F[1]).max() < 1e-14
+    assert np.abs(d["Ux"] - ub[0]).max() < 1e-14, np.abs(d["Ux"] - ub[0]).max()
+    assert np.abs(d["Uy"] - ub[1]).max() < 1e-14, np.abs(d["Uy"] - ub[1]).max()
+    # the force density is F drs delta(y - Y) on every node of a row (Eq. 15)
+    fx, fy = s.force_field()
+    prof = np.array([O.delta(kind, j - Y0) for j in range(fx.shape[0])])
+    assert np.abs(fx - F[0] * drs * prof[:, None]).max() < 1e-14
+    assert np.abs(fy - F[1] * drs * prof[:, None]).max() < 1e-14
+
+
+def test_flat_wall_further_passes_add_nothing():
+    """Algorithm 1 with NF = 3 on the same wall: the first pass already meets
+    U_b, so the increments of passes 2 and 3 vanish and F_b stays Eq. 20's."""
+    rho0, ustar, ub = 0.981, (-0.02, 0.015), (0.01, 0.0)
+    s, _, _ = _flat_wall(3, 0.35, rho0, ustar, ub, nf=3)
+    d = s.marker_diag(0)
+    assert np.abs(d["Fbx"] - 2 * rho0 * (ub[0] - ustar[0])).max() < 1e-14
+    assert np.abs(d["Fby"] - 2 * rho0 * (ub[1] - ustar[1])).max() < 1e-14
+    assert np.abs(d["Ux"] - ub[0]).max() < 1e-14 and np.abs(d["Uy"] - ub[1]).max() < 1e-14
