@@ -2,24 +2,26 @@
 // (Jiang & Liu, arXiv 1806.09403, Algorithm 1).
 //
 // State.  After every step the buffer holds the post-collision populations
-// g = f' (Eq. 5 right-hand side) as deviations from the lattice weights,
-// structure-of-arrays [9][ny][nxp].  The post-streaming populations of the
-// next step are obtained by a pull, f_a(x) = g_a(x - e_a), with the boundary
-// rules applied inside the pull.  Right after initialisation (or loading a
+// g = f' (Eq. 5 right-hand side) as deviations f_a - f_eq_a(1, U_r) from the
+// equilibrium of the reference state (unit density, reference velocity U_r),
+// structure-of-arrays, planar [9][ny][nxp] or row-interleaved [ny][9][nxp].
+// The post-streaming populations of the next step are obtained by a pull,
+// f_a(x) = g_a(x - e_a), with the boundary rules applied inside the pull.  Right after initialisation (or loading a
 // checkpoint) the buffer holds post-streaming populations instead and the
 // first step reads them in place ("local" mode).
 //
 // Kernels per step:
 //   ib_force       marker-parallel: pull the populations at every support
 //                  node, rho and u* (Eqs. 9-10), interpolate (Eq. 14), force
-//                  F_b = 2 rho_l (U_b - U*_l) (Eq. 20); the last block to
-//                  finish reduces the force on every body in FP64 (Eq. 27).
-//                  With NF > 1 it runs NF times (Algorithm 1 step 3); pass k
-//                  adds the force field of passes < k to u* (Eq. 11).
+//                  F_b = 2 rho_l (U_b - U*_l) (Eq. 20).  With NF > 1 it runs
+//                  NF times (Algorithm 1 step 3); pass k adds the force field
+//                  of passes < k to u* (Eq. 11).
 //   collide_stream node-parallel, one warp per 128-node row segment: pull,
 //                  node-centric spread of F_b onto band nodes (Eq. 15),
 //                  u = u* + f / (2 rho) (Eq. 11), f_eq (Eq. 6), Guo term
-//                  (Eq. 7), BGK collision (Eq. 5), vector stores.
+//                  (Eq. 7), BGK collision (Eq. 5), vector stores; block 0
+//                  then reduces the force on every body in FP64 (Eq. 27)
+//                  once the IB kernel has finished.
 #include "btdf_internal.cuh"
 #include "btdf_device.cuh"
 
