@@ -18,9 +18,10 @@
 * The same FP32 run with the convective outlet the paper uses: St, Cd and
   the lift amplitude of Table 3 within 2%.
 * The Strouhal number and mean drag of FP16 and BF16 storage against the FP32
-  path on the same domain: FP16 (scaled by 2^10) holds the 1 % bar over the
-  long run; BF16 (8-bit significand) drifts by a few percent in mean drag
-  and is held to 2 % in St and 5 % in Cd, the measured drift with margin.
+  path on the same domain, against the 1 % bar of the mixed-precision form:
+  FP16 (scaled by 2^10) holds it over the long run; BF16 (8-bit significand)
+  is expected to miss it (its mean drag drifts by a few percent), so its
+  check is an expected failure that prints the measured drift.
 """
 import math
 import os
@@ -145,7 +146,12 @@ def test_long_run_fp32_against_table3(long_runs):
     assert abs(cd_mean / t3["re200_cd_mean"] - 1.0) <= 0.10
 
 
-@pytest.mark.parametrize("name", ["f16", "bf16"])
+@pytest.mark.parametrize("name", [
+    "f16",
+    pytest.param("bf16", marks=pytest.mark.xfail(
+        strict=False, reason="BF16 storage (8-bit significand) misses the 1% bar of the "
+                             "mixed-precision form over long runs: its mean drag drifts from FP32")),
+])
 def test_long_run_mixed_against_fp32(long_runs, name):
     case, out = long_runs
     skip = LONG // 2
@@ -159,9 +165,9 @@ def test_long_run_mixed_against_fp32(long_runs, name):
           f"({abs(st / st32 - 1):.2e}), mean Cd {cd:.4f} vs {cd32:.4f} ({abs(cd / cd32 - 1):.2e}), "
           f"Cl amplitude {amp:.4f} vs {amp32:.4f} ({abs(amp / amp32 - 1):.2e})")
     assert periods >= 10
-    st_tol, cd_tol = (1e-2, 1e-2) if name == "f16" else (2e-2, 5e-2)
-    assert abs(st / st32 - 1.0) <= st_tol
-    assert abs(cd / cd32 - 1.0) <= cd_tol
+    # the bar of the mixed-precision form: St and mean Cd within 1 % of FP32
+    assert abs(st / st32 - 1.0) <= 1e-2
+    assert abs(cd / cd32 - 1.0) <= 1e-2
 
 
 def test_long_run_convective_outlet_against_table3():
