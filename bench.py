@@ -1,16 +1,22 @@
 """Benchmark of the BTDF-IB/LBM time step on GB300.
 
-Default workload: the paper-scale cylinder case, a 1600 x 800 D2Q9 lattice
-with one cylinder of D = 40 (126 markers) at Re = 200 (tau = 0.53), the
-3-point delta function and the paper's thickness drs = 1.9, FP32 arithmetic
-with FP32 deviation storage.  One step = the IB stage plus the fused
-collide-stream kernel.
+Default workload: an 8192 x 4096 D2Q9 lattice (33.55 M nodes, 2.4 GB of FP32
+populations per buffer pair) holding 400 cylinders of D = 20 (63 markers
+each, 25,200 markers) at seeded non-overlapping centres, Re = 200
+(tau = 0.515), the 3-point delta function and the paper's thickness
+drs = 1.9, FP32 arithmetic with FP32 deviation storage.  One step = the IB
+stage plus the fused collide-stream kernel.  The same lattice is then timed
+with FP16 and BF16 storage (mixed_precision), and the drag of every body over
+the oracle's sample is compared with the FP64 oracle (cd_err_vs_fp64).
+--workload paper selects the 1600 x 800 cylinder (Sec. 5.2 geometry, whose
+92 MB of populations fit in L2); --mode sweep runs that cylinder over the
+Re x delta grid.
 
-Timing: W untimed warm-up steps, then K timed steps.  The lattice (92 MB of
-populations) fits in L2, so L2 is flushed (512 MB written and read back) before every timed
-step and each step is bracketed by its own CUDA events on the launching
-stream; the flush is outside the events.  The fused kernel's duration comes
-from the library's own events around it (profiling mode).
+Timing: W untimed warm-up steps, then K timed steps.  L2 is flushed (512 MB
+written and read back) before every timed step and each step is bracketed by
+its own CUDA events on the launching stream; the flush is outside the
+events.  The fused kernel's duration comes from the library's own events
+around it (profiling mode).
 
 --impl reference times the FP64 CPU oracle on the host cores on the same
 workload (each step one full oracle step).
@@ -362,6 +368,84 @@ def adjoint_mode(args):
     return 0
 
 
+def measure_storage(B, case, storage, args, stream, world, flush_l2, barrier, layout,
+                    history_len, tune_steps=32):
+    """Autotunes the collide-stream variant for one storage format, then times
+    args.steps steps (L2 flushed before each, one event pair per step), then
+    the per-kernel durations in profiling mode.  Returns the context and a
+    dict of the measurements."""
+    import torch
+    lat = B.Lattice.from_case(case, storage=storage, stream=stream.cuda_stream,
+                              history_len=history_len, layout=layout)
+    nodes = case.nx * case.ny
+    lat.step(args.warmup)
+    lat.sync()
+    if args.variant == 0:
+        best, tms = lat.autotune(tune_steps, True)
+        tune = {VARIANT_NAMES[v]: t for v, t in tms.items()}
+    else:
+        best, tune = args.variant, {}
+        lat.tune(best, 0)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier()
+    for i in range(args.steps):
+        flush_l2()
+        ev[i][0].record(stream)
+        lat.step(1)
+        ev[i][1].record(stream)
+    barrier()
+    per_step = [a.elapsed_time(b) for a, b in ev]
+    # per-kernel durations: the library's events around each kernel, no overlap
+    lat.profile(True)
+    barrier()
+    for i in range(args.steps):
+        flush_l2()
+        lat.step(1)
+    ms_ib, ms_lbm, n_ib, n_lbm = lat.profile_read()
+    lat.profile(False)
+    # the same without the flush: in a run the IB kernel reads what the
+    # previous LBM kernel has just written
+    lat.profile(True)
+    lat.step(args.steps)
+    ms_ib_w, _, _, n_w = lat.profile_read()
+    lat.profile(False)
+    lat.sync()
+    ms = max_over_ranks(sum(per_step), world)
+    bpl = BYTES_PER_LU[storage]
+    return lat, {
+        "value": job_rate(nodes * args.steps, world, ms / 1e3) / 1e6,
+        "ms_sum": ms, "ms_per_step": ms / args.steps,
+        "ms_per_step_median": float(np.median(per_step)),
+        "kernel_ms_per_launch": ms_lbm / max(n_lbm, 1),
+        "ib_ms_per_step": ms_ib / max(n_lbm, 1),
+        "ib_ms_per_step_warm": ms_ib_w / max(n_w, 1),
+        "n_ib": n_ib, "n_lbm": n_lbm,
+        "achieved_gbs": bpl * nodes * n_lbm / (ms_lbm / 1e3) / 1e9,
+        "variant": VARIANT_NAMES[best], "tune": tune,
+    }
+
+
+def drag_error(B, case, storage, stream, sim_hist, n):
+    """Largest relative drag error of a fresh GPU run over the first n steps
+    against the FP64 oracle's history (every body), scaled as in the parity
+    tests: |dFx| / max(|Fx_ref(t)|, mean |Fx_ref|)."""
+    ref = B.Lattice.from_case(case, storage=storage, stream=stream.cuda_stream,
+                              history_len=max(n, 16))
+    ref.step(n)
+    worst = 0.0
+    for b, (rx, ry) in enumerate(sim_hist):
+        gx, gy = ref.forces(b, 0, n)
+        worst = max(worst, float(np.max(np.abs(gx - rx) / np.maximum(np.abs(rx), np.abs(rx).mean()))))
+    ref.close()
+    return worst
+
+
+VARIANT_NAMES = {1: "reg4", 2: "reg2", 3: "tma8x2", 4: "tma8x3", 5: "tma16x2", 6: "reg4pf",
+                 7: "reg2pf", 8: "reg1", 9: "reg2o", 10: "reg2o_l2pf", 11: "reg4_l2pf",
+                 12: "packed8", 13: "packed8_l2pf"}
+
+
 def our_arm(args):
     import torch
     world, rank, local = dist_setup(args)
@@ -377,10 +461,10 @@ def our_arm(args):
     storage = {"f32": 0, "f16": 1, "bf16": 2}[args.storage]
     stream = torch.cuda.current_stream()
     layout = {"rows": B.LAYOUT_ROWS, "planes": B.LAYOUT_PLANES}[args.layout]
-    lat = B.Lattice.from_case(case, storage=storage, stream=stream.cuda_stream,
-                              history_len=max(args.steps + args.warmup + 64, 4096), layout=layout)
     nodes = case.nx * case.ny
+    nmark = sum(len(b.X) for b in case.bodies)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    hist = max(args.steps + args.warmup + 64, 4096)
 
     def flush_l2():
         # Write a buffer larger than L2 (evicts the lattice), then read it so
@@ -389,56 +473,20 @@ def our_arm(args):
         flush.zero_()
         flush.sum()
 
-    # warm-up (graphs and direct launches both exercised)
-    lat.step(args.warmup)
-    lat.sync()
-
     def barrier():
         if world > 1:
             import torch.distributed as dist
             dist.barrier()
         torch.cuda.synchronize()
 
-    # ---- kernel variant: the library's autotuner times each candidate on
-    # this lattice (L2 evicted before every step, median of 32 steps) ----
-    names = {1: "reg4", 2: "reg2", 3: "tma8x2", 4: "tma8x3", 5: "tma16x2", 6: "reg4pf", 7: "reg2pf",
-             8: "reg1", 9: "reg2o", 10: "reg2o_l2pf", 11: "reg4_l2pf"}
-    if args.variant == 0:
-        best, tms = lat.autotune(32, True)
-        tune = {names[v]: t for v, t in tms.items()}
-    else:
-        best, tune = args.variant, {}
-        lat.tune(best, 0)
-    best_name = names[best]
-
-    # ---- timed region: K steps, L2 flushed before each, per-step events ----
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    barrier()
+    # ---- the timed line: autotuned variant, K steps, L2 flushed before each ----
     with ClockSampler(local) as clk:
-        for i in range(args.steps):
-            flush_l2()
-            ev[i][0].record(stream)
-            lat.step(1)
-            ev[i][1].record(stream)
-        barrier()
-    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world)
-    value = job_rate(nodes * args.steps, world, ms / 1e3) / 1e6
-
-    # ---- per-kernel durations (library events around each kernel, no overlap) ----
-    lat.profile(True)
-    barrier()
-    for i in range(args.steps):
-        flush_l2()
-        lat.step(1)
-    ms_ib, ms_lbm, n_ib, n_lbm = lat.profile_read()
-    lat.profile(False)
-    lat.sync()
+        lat, m = measure_storage(B, case, storage, args, stream, world, flush_l2, barrier, layout,
+                                 hist)
+    value = m["value"]
 
     # ---- roofline of the fused kernel ----
     peaks = measured_peaks()
-    bpl = BYTES_PER_LU[storage]
-    achieved = bpl * nodes * n_lbm / (ms_lbm / 1e3) / 1e9
     if peaks and peaks.get("hbm_gbs"):
         peak, peak_src = float(peaks["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
     else:
@@ -447,7 +495,7 @@ def our_arm(args):
 
     # ---- warm sustained rate through CUDA graphs (no flush) ----
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    nwarm = 2048
+    nwarm = max(64, min(2048, int(2.0e9 / nodes)))
     lat.step(64)
     e0.record(stream)
     lat.step(nwarm)
@@ -455,12 +503,14 @@ def our_arm(args):
     lat.sync()
     warm = nodes * nwarm / (e0.elapsed_time(e1) / 1e3) / 1e6
 
-    # ---- end to end through the C ABI with host buffers ----
-    nb = len(case.bodies[0].X) if case.bodies else 0
-    ubx = np.zeros(nb)
-    uby = np.zeros(nb)
-    fx = np.zeros(1)
-    fy = np.zeros(1)
+    # ---- end to end through the C ABI with host buffers: every step sets
+    # the prescribed velocity of every marker (H2D) and reads the force on
+    # every body (D2H), one copy each way ----
+    nbody = len(case.bodies)
+    ubx = np.zeros(nmark)
+    uby = np.zeros(nmark)
+    fx = np.zeros((1, max(nbody, 1)))
+    fy = np.zeros((1, max(nbody, 1)))
     ne2e = min(args.steps, 2000)
     tot = 0.0
     barrier()
@@ -468,20 +518,32 @@ def our_arm(args):
         flush_l2()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        if nb:
-            lat.set_marker_velocity(0, ubx, uby)           # H2D of the step's input
+        if nbody:
+            lat.set_marker_velocity(-1, ubx, uby)           # H2D of the step's input
         lat.step(1)
-        if nb:
-            lat.forces(0, lat.steps - 1, 1, out=(fx, fy))  # D2H of the step's result
+        if nbody:
+            lat.forces(-1, lat.steps - 1, 1, out=(fx, fy))  # D2H of the step's result
         else:
             lat.sync()
         tot += time.perf_counter() - t0
     tot = max_over_ranks(tot, world)
     e2e = job_rate(nodes * ne2e, world, tot) / 1e6
+    lat.close()
+
+    # ---- the 16-bit storage forms on the same lattice ----
+    mixed = {}
+    if args.mixed and storage == 0:
+        for name, st in (("f16", 1), ("bf16", 2)):
+            l2, mm = measure_storage(B, case, st, args, stream, world, flush_l2, barrier, layout,
+                                     hist)
+            l2.close()
+            mm["frac"] = mm["achieved_gbs"] / peak
+            mm["traffic"] = ncu_traffic(args.workload, st)
+            mixed[name] = mm
 
     # ---- FP64 oracle on the host cores, and drag error against it ----
     cpu = None
-    cd_err = None
+    cd_err = {}
     if rank == 0 and not args.no_cpu_baseline:
         threads = min(os.cpu_count() or 1, 64)
         sim, n_or, el = run_oracle_sample(case, args.cpu_seconds, threads)
@@ -490,46 +552,103 @@ def our_arm(args):
                "sample": f"first {n_or} steps of the same workload ({el:.1f} s of CPU time, "
                          f"OpenMP over rows)"}
         if case.bodies:
-            ref = B.Lattice.from_case(case, storage=storage, stream=stream.cuda_stream,
-                                      history_len=max(n_or, 16))
-            ref.step(n_or)
-            gx, _ = ref.forces(0, 0, n_or)
-            rx, _ = sim.history(0, 0, n_or)
-            cd_err = float(np.max(np.abs(gx - rx) / np.maximum(np.abs(rx), np.abs(rx).mean())))
-            ref.close()
+            sim_hist = [sim.history(b, 0, n_or) for b in range(len(case.bodies))]
+            for name, st in (("f32", 0), ("f16", 1), ("bf16", 2)):
+                if st == storage or name in mixed:
+                    cd_err[name] = drag_error(B, case, st, stream, sim_hist, n_or)
+            cd_err["steps"] = n_or
+            cd_err["bodies"] = len(case.bodies)
+        del sim
 
     if rank != 0:
         return 0
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms_per_step"],
+        "ms_per_step_median": m["ms_per_step_median"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {0: "f32", 1: "f32 (f16 storage)", 2: "f32 (bf16 storage)"}[storage],
         "data": "synthetic",
         "config": {"workload": desc, "nx": case.nx, "ny": case.ny,
                    "storage": args.storage, "layout": args.layout,
-                   "markers": sum(len(b.X) for b in case.bodies),
-                   "l2": "flushed before every timed step (512 MB written, then read back so "
+                   "markers": nmark,
+                   "l2": ("inputs (%.2f GB of populations) larger than L2; " % (
+                       2 * BYTES_PER_LU[storage] / 2 * nodes / 1e9) if nodes * 36 > 256e6 else "") +
+                         "flushed before every timed step (512 MB written, then read back so "
                          "the lines left in L2 are clean); flush outside the per-step CUDA events",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "collide_stream", "bytes_per_lu": bpl,
-                     "kernel_ms_per_launch": ms_lbm / max(n_lbm, 1),
-                     "ib_ms_per_step": ms_ib / max(n_lbm, 1), "peak_source": peak_src},
+        "roofline": {"bound": "hbm", "achieved": m["achieved_gbs"], "peak": peak, "unit": "GB/s",
+                     "frac": m["achieved_gbs"] / peak, "traffic": traffic,
+                     "kernel": "collide_stream", "bytes_per_lu": BYTES_PER_LU[storage],
+                     "units_per_launch": nodes,
+                     "kernel_ms_per_launch": m["kernel_ms_per_launch"],
+                     "ib_ms_per_step": m["ib_ms_per_step"],
+                     "ib_ms_per_step_warm_l2": m["ib_ms_per_step_warm"], "ib_markers": nmark,
+                     "peak_source": peak_src},
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e, "unit": "MLUPS", "h2d_bytes_per_step": 16 * nb,
-                "d2h_bytes_per_step": 16 if nb else 0,
-                "how": "per step: marker velocities H2D, one step, body force D2H, synchronous"},
-        "gpu_launches": int(args.steps * (n_ib + n_lbm) // max(n_lbm, 1)),
-        "kernel_variant": {"chosen": best_name, "ms_per_step_flushed": tune,
+        "e2e": {"value": e2e, "unit": "MLUPS", "h2d_bytes_per_step": 16 * nmark,
+                "d2h_bytes_per_step": 16 * nbody,
+                "how": "per step: every marker's prescribed velocity H2D (one copy), one step, "
+                       "the force on every body D2H (one copy), synchronous"},
+        "gpu_launches": int(args.steps * (m["n_ib"] + m["n_lbm"]) // max(m["n_lbm"], 1)),
+        "kernel_variant": {"chosen": m["variant"], "ms_per_step_flushed": m["tune"],
                            "tuner": "btdf_autotune: median of 32 steps per variant, L2 evicted "
                                     "before each"},
         "clocks": clk.summary(),
         "graph_warm_mlups": warm,
-        "cd_err_vs_fp64": cd_err,
+        "cd_err_vs_fp64": cd_err or None,
+        "mixed_precision": {k: {"value": v["value"], "unit": "MLUPS",
+                                "ms_per_step": v["ms_per_step"],
+                                "ms_per_step_median": v["ms_per_step_median"],
+                                "kernel_ms_per_launch": v["kernel_ms_per_launch"],
+                                "achieved_gbs": v["achieved_gbs"], "frac": v["frac"],
+                                "traffic": v["traffic"], "bytes_per_lu": 36,
+                                "variant": v["variant"], "speedup_vs_f32": v["value"] / value}
+                            for k, v in mixed.items()} or None,
     }
     print(json.dumps(line))
+    return 0
+
+
+def sweep_mode(args):
+    """The 1600 x 800 cylinder over Re in {0.1, 40, 200} and the 2-, 3- and
+    4-point delta functions (each with its thickness of Sec. 4.4): MLUPS per
+    point, L2 flushed before every timed step, autotuned variant."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import workloads as W
+    from paper_1806_09403_gb300 import btdf as B
+    storage = {"f32": 0, "f16": 1, "bf16": 2}[args.storage]
+    layout = {"rows": B.LAYOUT_ROWS, "planes": B.LAYOUT_PLANES}[args.layout]
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def flush_l2():
+        flush.zero_()
+        flush.sum()
+
+    def barrier():
+        torch.cuda.synchronize()
+
+    peaks = measured_peaks() or {}
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    points = []
+    for re_ in (0.1, 40.0, 200.0):
+        for delta in (2, 3, 4):
+            case = W.paper_cylinder(re=re_, delta=delta)
+            lat, m = measure_storage(B, case, storage, args, stream, 1, flush_l2, barrier, layout,
+                                     max(args.steps + args.warmup + 64, 4096), tune_steps=16)
+            lat.close()
+            points.append({"re": re_, "delta": delta, "tau": case.tau, "mlups": m["value"],
+                           "ms_per_step_median": m["ms_per_step_median"],
+                           "kernel_ms_per_launch": m["kernel_ms_per_launch"],
+                           "ib_ms_per_step": m["ib_ms_per_step"],
+                           "kernel_frac": m["achieved_gbs"] / peak, "variant": m["variant"]})
+    print(json.dumps({"mode": "sweep", "workload": "cylinder 1600x800, D=40, 126 markers, "
+                      "Re x delta grid, drs = 1.4 / 1.9 / 2.6", "storage": args.storage,
+                      "steps": args.steps, "peak_gbs": peak, "points": points}))
     return 0
 
 
@@ -539,13 +658,16 @@ def main():
     ap.add_argument("--steps", type=int, default=10000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="paper", choices=["paper", "small", "mid", "large"])
+    ap.add_argument("--workload", default="large", choices=["paper", "small", "mid", "large"])
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-seconds", type=float, default=90.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="bench", choices=["bench", "kernel", "batch", "adjoint"])
-    ap.add_argument("--variant", type=int, default=0, choices=list(range(12)))
+    ap.add_argument("--mode", default="bench",
+                    choices=["bench", "kernel", "batch", "adjoint", "sweep"])
+    ap.add_argument("--no-mixed", dest="mixed", action="store_false",
+                    help="skip the FP16 / BF16 storage lines of the default bench")
+    ap.add_argument("--variant", type=int, default=0, choices=list(range(14)))
     ap.add_argument("--layout", default="rows", choices=["rows", "planes"])
     args = ap.parse_args()
     if args.warmup < 3:
@@ -558,6 +680,8 @@ def main():
         return batch_mode(args)
     if args.mode == "adjoint":
         return adjoint_mode(args)
+    if args.mode == "sweep":
+        return sweep_mode(args)
     return our_arm(args)
 
 

@@ -143,8 +143,10 @@ int btdf_init_fields(btdf_ctx *ctx, const double *rho, const double *ux, const d
  * the configured delta: 1.4, 1.9, 2.6 for 2, 3, 4 points, 2.6 for the cosine
  * kernel).  Interpolation weights delta(x_e - X) delta(y_e - Y) (Eq. 14) are
  * evaluated once here in FP64; markers are static.  Every marker's support
- * must lie at least partly inside the lattice.  *body_id receives the index.
- * Errors: EINVAL (n < 1, ds <= 0, marker outside the lattice). */
+ * must lie at least partly inside the lattice; under BTDF_BCX_CONVECTIVE no
+ * support may reach the outlet column x = nx-1.  *body_id receives the index.
+ * Errors: EINVAL (n < 1, ds <= 0, marker outside the lattice, support on the
+ * convective outlet column). */
 int btdf_add_markers(btdf_ctx *ctx, int32_t n, const double *X, const double *Y,
                      const double *Ubx, const double *Uby, double ds, double drs,
                      int32_t *body_id);
@@ -167,7 +169,9 @@ int btdf_add_cylinder(btdf_ctx *ctx, double cx, double cy, double D, int32_t n, 
                       int32_t *body_id);
 
 /* Replaces the prescribed marker velocities U_b of one body (host arrays of
- * that body's marker count, read before the call returns).  The upload is
+ * that body's marker count, read before the call returns), or, with
+ * body = -1, of every body at once (arrays of all markers, in the order the
+ * bodies were added; one copy to the device).  The upload is
  * asynchronous on the context stream through one of four page-locked
  * staging slots; a call waits only when the upload four calls back has not
  * run yet. */
@@ -183,7 +187,10 @@ int btdf_set_inflow(btdf_ctx *ctx, double u_in);
 /* Moves the markers of one body to (X[l], Y[l]) (host arrays of the body's
  * marker count) and re-evaluates its weights and the spreading table; ds,
  * drs and the velocities are kept.  The force history restarts at the
- * current step.  Synchronizes.  Errors: EINVAL (bad body, marker outside). */
+ * current step.  Synchronizes.  The positions are checked as in
+ * btdf_add_markers (convective outlet column included) before anything
+ * changes.  Errors: EINVAL (bad body, marker outside, support on the
+ * convective outlet column). */
 int btdf_move_markers(btdf_ctx *ctx, int32_t body, const double *X, const double *Y);
 
 /* Advances nsteps time steps (Algorithm 1), asynchronously on the context
@@ -195,15 +202,18 @@ int btdf_step(btdf_ctx *ctx, int64_t nsteps);
 int btdf_sync(btdf_ctx *ctx);
 
 /* Force on one body (Eq. 27, force exerted by the fluid on the body) for the
- * steps first .. first+n-1, into host arrays Fx, Fy of n doubles.  The steps
- * must have been taken and must still be inside the device history ring.
- * Synchronizes.  Errors: EINVAL (body or step range). */
+ * steps first .. first+n-1, into host arrays Fx, Fy of n doubles; with
+ * body = -1 the forces on every body, n x nbody doubles each, step-major
+ * (Fx[i * nbody + b]).  The steps must have been taken and must still be
+ * inside the device history ring.  Synchronizes.  Errors: EINVAL (body or
+ * step range). */
 int btdf_read_forces(btdf_ctx *ctx, int32_t body, int64_t first, int64_t n,
                      double *Fx, double *Fy);
 
 /* As btdf_read_forces, without waiting: enqueues the copy of the steps
- * first .. first+n-1 into F[2 i] = Fx, F[2 i + 1] = Fy on the context
- * stream and returns.  F must stay valid until the stream reaches the copy
+ * first .. first+n-1 into F[2 i] = Fx, F[2 i + 1] = Fy (body = -1: into
+ * F[2 (i * nbody + b)], F[2 (i * nbody + b) + 1]) on the context stream and
+ * returns.  F must stay valid until the stream reaches the copy
  * (btdf_sync); page-locked memory (cudaMallocHost, a pinned torch tensor)
  * makes it a DMA transfer that overlaps host work, pageable memory makes
  * the call wait for the copy.  Device status is reported by btdf_sync. */
@@ -225,10 +235,16 @@ int64_t btdf_step_count(const btdf_ctx *ctx);
 
 /* Checkpoint of the populations and the step counter (not the force
  * history), plus the outlet column buffer under the convective outlet.
+ * Byte image: a 48-byte header (uint64 magic; int32 nx, ny, nxp, storage;
+ * int32 at byte 24: 1 if the populations are post-streaming, 0 if
+ * post-collision; int32 layout; int64 step counter; double at byte 40: the
+ * reference velocity u_ref of the stored deviations, i.e. the creation-time
+ * u_in), then the population buffer in the device layout, then the outlet
+ * column ([9][ny] floats) under the convective outlet.
  * btdf_state_size gives the byte count; save copies to a host buffer of at
  * least that size; load restores a checkpoint of a context with the same nx,
- * ny, storage, layout and x boundary.  Errors: EINVAL (size or shape
- * mismatch). */
+ * ny, storage, layout, x boundary and creation-time u_in.  Errors: EINVAL
+ * (size, shape or reference-velocity mismatch). */
 int btdf_state_size(btdf_ctx *ctx, size_t *bytes);
 int btdf_save_state(btdf_ctx *ctx, void *dst, size_t cap, size_t *used);
 int btdf_load_state(btdf_ctx *ctx, const void *src, size_t len);
@@ -244,7 +260,7 @@ int btdf_profile_read(btdf_ctx *ctx, double *ms_ib, double *ms_lbm, int64_t *lau
 
 /* Number of collide-stream variants, 0 (automatic) included: the length of
  * btdf_autotune's ms output. */
-#define BTDF_VARIANT_COUNT 12
+#define BTDF_VARIANT_COUNT 14
 
 /* Variant of the fused collide-stream kernel.  Results do not depend on it.
  *   0 automatic (2 for FP32 storage, 1 for FP16 / BF16)
@@ -260,15 +276,30 @@ int btdf_profile_read(btdf_ctx *ctx, double *ms_ib, double *ms_lbm, int64_t *lau
  *  10 as 9, and each warp prefetches into L2 the row segment that a warp
  *     half a wave later will process
  *  11 as 1, with the L2 prefetch of 10
+ *  12 16-bit storage: 8 nodes per lane over 256-node row segments, the nine
+ *     planes read as 16-byte vectors and kept packed two nodes per word;
+ *     segments with boundary rules or forcing take the 4-node path of 1
+ *     (FP32 storage: as 1)
+ *  13 as 12, with the L2 prefetch of 10 (FP32 storage: as 11)
  * grid_blocks caps the grid, counted in blocks of the variant: 256 threads,
- * or 128 for variant 2 and, with FP16 / BF16 storage, variants 1 and 8-11.
+ * or 128 for variant 2 and, with FP16 / BF16 storage, variants 1 and 8-13.
  * 0 = default:
- * one 32 x NPL-node row segment per warp for variants 1, 2 and 8-11, so the
+ * one 32 x NPL-node row segment per warp for variants 1, 2 and 8-13, so the
  * block scheduler balances the SMs; SM count x resident blocks per SM for
  * the persistent variants 3-7.
  * Synchronizes and drops cached CUDA graphs.
  * Errors: EINVAL (unknown variant, TMA variant without tensor maps). */
 int btdf_tune(btdf_ctx *ctx, int32_t variant, int32_t grid_blocks);
+
+/* Bound of the TMA-tiled variants' (3-5) per-stage waits, in polls of the
+ * stage's mbarrier: polls < 0 restores the default (about a second of
+ * polling); 0 makes every such wait give up at once.  A wait that gives up
+ * records BTDF_ETIMEOUT in the status word (reported by the next btdf_sync),
+ * and its CTA waits, with the default bound, for the copies it has in flight
+ * before it leaves; the populations of that step are then invalid.  Meant for
+ * testing the timeout path of failure detection.  Synchronizes and drops
+ * cached CUDA graphs. */
+int btdf_set_wait_limit(btdf_ctx *ctx, int32_t polls);
 
 /* Bytes of device memory the context holds. */
 int btdf_device_bytes(const btdf_ctx *ctx, size_t *bytes);
@@ -371,9 +402,9 @@ const char *btdf_batch_last_error(const btdf_batch *b);
 /* ---- IB force stage without device allocation ----------------------------
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot call cudaMalloc: code that runs inside another framework's memory
- * budget (a caching allocator owns the device memory), code issued while a
- * CUDA stream is being captured into a graph (allocation is not permitted
- * there), or real-time loops that must not enter the driver's allocator.
+ * budget (a caching allocator owns the device memory), or real-time loops
+ * that must not enter the driver's allocator.  The call copies its host
+ * inputs from pageable memory and synchronizes `stream` before returning.
  *
  * For one body of n markers it runs the IB stage of one step on a population
  * buffer the caller owns: interpolation of rho and u* to the markers
@@ -381,34 +412,40 @@ const char *btdf_batch_last_error(const btdf_batch *b);
  * the force on the body F_p = -sum F_b ds drs in FP64 (Eq. 27).  It uses the
  * same kernel as btdf_step's IB stage.
  *   cfg    lattice description (nx, ny, u_in, delta, storage, bc_x, bc_y,
- *          layout; tau, nf, history_len and g are not used).
+ *          layout; tau, nf, history_len and g are not used).  cfg->u_in is
+ *          the inlet speed the pull's inlet rule extrapolates to.
  *   pops   device pointer to populations in the library's layout: the
- *          storage type, deviations f_a - f_eq_a(1, (u_in, 0)), rows of
+ *          storage type, deviations f_a - f_eq_a(1, (u_ref, 0)), rows of
  *          nxp = nx rounded up to 32, planar or row-interleaved per
- *          cfg->layout.  This is the byte image btdf_save_state writes after
- *          its 40-byte header.
+ *          cfg->layout, aligned to the storage element.  This is the byte
+ *          image btdf_save_state writes after its 48-byte header.
  *   pull   0: pops holds post-streaming populations; 1: post-collision ones
  *          (streaming and the boundary rules are applied while reading).  A
  *          checkpoint's header says which (its int32 at byte 24 is 1 for
  *          post-streaming).
+ *   u_ref  reference velocity (u_ref, 0) of the stored deviations: the
+ *          creation-time u_in of the context that wrote them (a checkpoint's
+ *          double at byte 40); it differs from cfg->u_in after
+ *          btdf_set_inflow.
  *   X, Y, Ubx, Uby, ds, drs  as in btdf_add_markers (host arrays of n
  *          doubles; Ubx/Uby may be NULL; drs <= 0 takes Sec. 4.4's value).
- *   Fb     device output, 2n floats (F_b per marker, x and y interleaved).
+ *   Fb     device output, 2n floats (F_b per marker, x and y interleaved),
+ *          8-byte aligned.
  *   Fp     host output, 2 doubles (force on the body).
- *   stream cudaStream_t to run on (NULL = legacy default stream); the call
- *          synchronizes it before returning.
+ *   stream cudaStream_t to run on (NULL = legacy default stream).
  * No device memory is allocated: the marker tables and the reduction scratch
  * live in one file-scope device array of about 320 KB, which every GPU that
  * loads the library holds until the process exits.  n may not exceed
- * BTDF_STATIC_MAX_MARKERS (EINVAL).  The first call on a device looks up that
- * array's device address (cudaGetSymbolAddress); make that first call before
- * any stream capture.  Every call reuses the same array, so calls that
- * overlap on the GPU (two streams, two host threads) race: serialize them.
- * Errors: EINVAL (arguments, n out of range), ECUDA, EUNSTABLE (density or
- * force at a marker non-positive or non-finite). */
+ * BTDF_STATIC_MAX_MARKERS (EINVAL).  The first call on a device (and the
+ * first after its CUDA context was re-created) looks up that array's device
+ * address with cudaGetSymbolAddress.  Every call reuses the same array, so
+ * calls that overlap on the GPU (two streams, two host threads) race:
+ * serialize them.
+ * Errors: EINVAL (arguments, n out of range, misaligned Fb or pops), ECUDA,
+ * EUNSTABLE (density or force at a marker non-positive or non-finite). */
 #define BTDF_STATIC_MAX_MARKERS 2048
-int btdf_ib_forces_static(const btdf_config *cfg, const void *pops, int32_t pull, int32_t n,
-                          const double *X, const double *Y, const double *Ubx,
+int btdf_ib_forces_static(const btdf_config *cfg, const void *pops, int32_t pull, double u_ref,
+                          int32_t n, const double *X, const double *Y, const double *Ubx,
                           const double *Uby, double ds, double drs, float *Fb, double *Fp,
                           void *stream);
 

@@ -39,10 +39,11 @@ EXPORTS = [
     "btdf_batch_last_error", "btdf_set_inflow", "btdf_move_markers", "btdf_adjoint_forward",
     "btdf_adjoint_backward", "btdf_adjoint_release", "btdf_autotune", "btdf_batch_autotune",
     "btdf_read_forces_async", "btdf_add_cylinder", "btdf_set_boundary_velocity",
+    "btdf_set_wait_limit",
 ]
 STATIC_MAX_MARKERS = 2048
-VARIANT_COUNT = 12          # BTDF_VARIANT_COUNT: variants 0 (automatic) .. 11, see btdf_tune
-STATE_HEADER_BYTES = 40
+VARIANT_COUNT = 14          # BTDF_VARIANT_COUNT: variants 0 (automatic) .. 13, see btdf_tune
+STATE_HEADER_BYTES = 48
 
 
 class btdf_config(C.Structure):
@@ -112,8 +113,9 @@ def lib() -> C.CDLL:
     L.btdf_status_string.argtypes = [C.c_int]
     L.btdf_status_string.restype = C.c_char_p
     L.btdf_version.restype = C.c_int
-    L.btdf_ib_forces_static.argtypes = [C.POINTER(btdf_config), vp, C.c_int32, C.c_int32, _dp, _dp,
-                                        vp, vp, C.c_double, C.c_double, vp, _dp, vp]
+    L.btdf_ib_forces_static.argtypes = [C.POINTER(btdf_config), vp, C.c_int32, C.c_double,
+                                        C.c_int32, _dp, _dp, vp, vp, C.c_double, C.c_double, vp,
+                                        _dp, vp]
     L.btdf_batch_create.argtypes = [C.POINTER(btdf_config), C.c_int32, vp, C.POINTER(vp)]
     L.btdf_batch_destroy.argtypes = [vp]
     L.btdf_batch_init_fields.argtypes = [vp, C.c_int32, _dp, _dp, _dp]
@@ -129,6 +131,7 @@ def lib() -> C.CDLL:
     L.btdf_batch_read_forces.argtypes = [vp, C.c_int32, C.c_int64, C.c_int64, vp, vp]
     L.btdf_batch_read_field.argtypes = [vp, C.c_int32, C.c_int32, vp, C.c_int32]
     L.btdf_set_inflow.argtypes = [ctxp, C.c_double]
+    L.btdf_set_wait_limit.argtypes = [ctxp, C.c_int32]
     L.btdf_move_markers.argtypes = [ctxp, C.c_int32, _dp, _dp]
     L.btdf_adjoint_forward.argtypes = [ctxp, C.c_int64, C.c_int32, C.c_int32, C.c_double,
                                        C.POINTER(C.c_double)]
@@ -165,17 +168,19 @@ def btdf_version() -> int:
 
 
 def btdf_ib_forces_static(cfg: btdf_config, pops_ptr: int, pull: bool, X, Y, ds, Ubx=None,
-                          Uby=None, drs=0.0, fb_ptr: int = 0, stream: int = 0):
+                          Uby=None, drs=0.0, fb_ptr: int = 0, stream: int = 0, u_ref=None):
     """IB force stage of one body on a caller-owned device population buffer,
-    without any device allocation (see include/btdf.h).  Returns
+    without any device allocation (see include/btdf.h).  u_ref is the
+    reference velocity of the stored deviations (default: cfg.u_in).  Returns
     (status, (Fx, Fy)); F_b per marker is written to the device pointer fb_ptr."""
     X = np.ascontiguousarray(X, dtype=np.float64)
     Y = np.ascontiguousarray(Y, dtype=np.float64)
     ubx = None if Ubx is None else np.ascontiguousarray(Ubx, dtype=np.float64)
     uby = None if Uby is None else np.ascontiguousarray(Uby, dtype=np.float64)
     Fp = np.zeros(2)
-    rc = lib().btdf_ib_forces_static(C.byref(cfg), C.c_void_p(pops_ptr), 1 if pull else 0, len(X),
-                                     X, Y, None if ubx is None else ubx.ctypes.data,
+    ur = float(cfg.u_in if u_ref is None else u_ref)
+    rc = lib().btdf_ib_forces_static(C.byref(cfg), C.c_void_p(pops_ptr), 1 if pull else 0, ur,
+                                     len(X), X, Y, None if ubx is None else ubx.ctypes.data,
                                      None if uby is None else uby.ctypes.data, float(ds),
                                      float(drs or 0.0), C.c_void_p(fb_ptr), Fp,
                                      C.c_void_p(stream or None))
@@ -265,6 +270,8 @@ class Lattice:
         return bid.value
 
     def set_marker_velocity(self, body, Ubx, Uby):
+        """Prescribed velocities of one body's markers, or with body = -1 of
+        every marker (in the order the bodies were added)."""
         self._check(lib().btdf_set_marker_velocity(self._ctx, body, _f64(Ubx), _f64(Uby)),
                     "btdf_set_marker_velocity")
 
@@ -279,9 +286,12 @@ class Lattice:
         return lib().btdf_step_count(self._ctx)
 
     def forces(self, body=0, first=0, n=None, out=None):
+        """Body force (Eq. 27) of steps first .. first+n-1: arrays of n, or,
+        with body = -1, of shape (n, bodies) (every body per step)."""
         n = self.steps - first if n is None else n
+        shape = (n, len(self.body_markers)) if body == -1 else (n,)
         if out is None:
-            out = (np.zeros(n), np.zeros(n))
+            out = (np.zeros(shape), np.zeros(shape))
         Fx, Fy = out
         self._check(lib().btdf_read_forces(self._ctx, body, first, n, Fx.ctypes.data,
                                            Fy.ctypes.data), "btdf_read_forces")
@@ -352,6 +362,10 @@ class Lattice:
         self._check(lib().btdf_autotune(self._ctx, int(steps), 1 if flush_l2 else 0, C.byref(ch),
                                         ms.ctypes.data), "btdf_autotune")
         return ch.value, {v: float(ms[v]) for v in range(1, VARIANT_COUNT) if ms[v] >= 0}
+
+    def set_wait_limit(self, polls):
+        """Polls before a TMA stage wait gives up (< 0: the default bound)."""
+        self._check(lib().btdf_set_wait_limit(self._ctx, int(polls)), "btdf_set_wait_limit")
 
     def set_inflow(self, u_in):
         self._check(lib().btdf_set_inflow(self._ctx, float(u_in)), "btdf_set_inflow")

@@ -84,7 +84,7 @@ namespace {
 constexpr int kGraphSteps = 64;          // steps per replayed CUDA graph (even)
 constexpr int kFullGrid = 1 << 30;       // grid cap meaning "one row segment per warp"
 constexpr int kStageSlots = 4;           // pinned staging slots for marker velocities
-constexpr uint64_t kStateMagic = 0x3130465444544242ull;
+constexpr uint64_t kStateMagic = 0x3230465444544242ull;   // "BBTDTF02"
 
 struct Body {
     int first = 0, n = 0;
@@ -93,12 +93,16 @@ struct Body {
     std::vector<double> wsum;      // sum of each marker's weights (filled by rebuild)
 };
 
+// Checkpoint header (48 bytes).  u_ref is the reference velocity the stored
+// deviations are relative to (the creation-time u_in of the context).
 struct StateHeader {
     uint64_t magic;
     int32_t nx, ny, nxp, storage;
     int32_t poststream, layout;
     int64_t steps;
+    double u_ref;
 };
+static_assert(sizeof(StateHeader) == 48, "checkpoint header layout");
 
 int support_width(int kind) { return kind == 2 ? 2 : kind == 3 ? 3 : (kind == 4 || kind == 5) ? 4 : 0; }
 
@@ -190,7 +194,7 @@ struct btdf_ctx {
 
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     long long pf_grid[2] = {1, 1};                 // software-pipelined kernel [npl 4/2]
-    long long pf_units[2][2] = {};                 // L2 prefetch distance of variants 10, 11 [local/pull]
+    long long pf_units[3][2] = {};                 // L2 prefetch distance of variants 10, 11, 13 [local/pull]
     long long tma_grid[kVarCount] = {};  // persistent grid of each TMA variant
     int variant = kVarAuto;              // LBM kernel variant (btdf_tune)
     int grid_override = 0;               // 0: SMs x resident blocks
@@ -212,6 +216,7 @@ struct btdf_ctx {
     long long marker_gen = 0;          // bumped by every rebuild of the marker tables
     AdjointTape tape;
     double2* tune_hist = nullptr;      // one-slot force ring used while btdf_autotune times steps
+    int wait_polls = -1;               // btdf_set_wait_limit (< 0: default bound)
 };
 
 namespace {
@@ -343,6 +348,11 @@ LatticeParams lattice_params(const btdf_ctx* ctx) {
             p.womp[a] = make_float2(p.wom[a], p.wom[a]);
         }
         p.omop = make_float2(p.one_m_omega, p.one_m_omega);
+        for (int a = 0; a < 9; a++) {   // the class tables of the packed kernel
+            p.c1e[ex(a) + 1] = p.c1p[a];
+            p.kre[ex(a) + 1] = p.krp[a];
+            p.womw[a == 0 ? 0 : (a < 5 ? 1 : 2)] = p.womp[a];
+        }
     }
     p.nwork = (long long)ctx->cfg.ny * ctx->nseg;
     // planar: [9][ny][nxp]; row-interleaved: [ny][9][nxp]
@@ -357,6 +367,7 @@ LatticeParams lattice_params(const btdf_ctx* ctx) {
     p.F = ctx->d_F[(ctx->cfg.nf - 1) % 2];
     p.step = ctx->d_step;
     p.status = ctx->d_status;
+    p.wait_polls = ctx->wait_polls;
     p.nbody = ctx->nmark > 0 ? (int)ctx->bodies.size() : 0;
     p.hist_len = ctx->cfg.history_len;
     p.body_ptr = ctx->d_body_ptr;
@@ -401,7 +412,10 @@ int enqueue_step(btdf_ctx* ctx, cudaStream_t st, bool pull, int cur, bool prof) 
             q.rhol = ctx->d_rhol;
             q.first_pass = k == 1;
             q.status = ctx->d_status;
-            CK(launch_ib_force(ctx->cfg.storage, pull, ctx->width, ctx->g[cur], p, q, st));
+            // Without profiling events in between, each IB pass is a
+            // programmatic dependent of the kernel before it: it loads its
+            // marker tables while that kernel drains, then waits for it.
+            CK(launch_ib_force(ctx->cfg.storage, pull, ctx->width, ctx->g[cur], p, q, !prof, st));
         }
     }
     if (prof) CK(cudaEventRecord(e1, st));
@@ -429,8 +443,8 @@ int enqueue_step(btdf_ctx* ctx, cudaStream_t st, bool pull, int cur, bool prof) 
                          : pf                   ? (int)ctx->pf_grid[v == kVarReg2Pf ? 1 : 0]
                                                 : kFullGrid;
         LatticeParams q = p;
-        if (v == kVarReg2OccPf || v == kVarReg4L2Pf)
-            q.pf_ahead = (int)ctx->pf_units[v == kVarReg4L2Pf ? 1 : 0][pull ? 1 : 0];
+        if (v == kVarReg2OccPf || v == kVarReg4L2Pf || v == kVarPackedL2Pf)
+            q.pf_ahead = (int)ctx->pf_units[v == kVarReg2OccPf ? 0 : v == kVarReg4L2Pf ? 1 : 2][pull ? 1 : 0];
         CK(launch_collide_stream(ctx->cfg.storage, pull, v, ctx->g[cur], ctx->g[1 - cur], q, grid, pdl, st));
     }
     if (prof) CK(cudaEventRecord(e2, st));
@@ -587,6 +601,9 @@ int rebuild_markers(btdf_ctx* ctx) {
 size_t outlet_bytes(const btdf_ctx* ctx) { return ctx->d_outlet ? sizeof(float) * 9 * ctx->cfg.ny : 0; }
 
 // Marker positions must be finite and their support must touch the lattice.
+// Under the convective outlet no support may reach the outlet column: the IB
+// kernel would read the outlet column buffer while the overlapping LBM kernel
+// rewrites it.  Every path that places markers (add, move) goes through here.
 int check_positions(btdf_ctx* ctx, int n, const double* X, const double* Y) {
     const int nx = ctx->cfg.nx, ny = ctx->cfg.ny;
     const double half = 0.5 * ctx->width;
@@ -599,6 +616,10 @@ int check_positions(btdf_ctx* ctx, int n, const double* X, const double* Y) {
         if ((ctx->cfg.bc_x == kBcxPeriodic && std::fabs(X[l]) > 1e9) ||
             (ctx->cfg.bc_y == kBcyPeriodic && std::fabs(Y[l]) > 1e9))
             return fail(ctx, BTDF_EINVAL, "marker position out of range");
+        // last support column: floor(X - w/2) + w
+        if (ctx->cfg.bc_x == BTDF_BCX_CONVECTIVE &&
+            (int)std::floor(X[l] - half) + ctx->width > nx - 2)
+            return fail(ctx, BTDF_EINVAL, "a marker support reaches the convective outlet column");
     }
     return BTDF_OK;
 }
@@ -639,7 +660,7 @@ int tape_step(btdf_ctx* ctx, int64_t n, const float* gin, float* gout, cudaStrea
     q.rhol = T.rhol;
     q.first_pass = 1;
     q.status = ctx->d_status;
-    CK(launch_ib_force(kStoreF32, pull, ctx->width, gin, p, q, st));
+    CK(launch_ib_force(kStoreF32, pull, ctx->width, gin, p, q, false, st));
     CK(launch_collide_stream(kStoreF32, pull, kVarReg4, gin, gout, p, kFullGrid, true, st));
     return BTDF_OK;
 }
@@ -799,6 +820,28 @@ int tape_alloc(btdf_ctx* ctx, int nck, int every, int64_t nsteps) {
     return BTDF_OK;
 }
 
+// Copies steps first .. first+n-1 of the force history into dst: one
+// double2 per step for one body, or, with body -1, nbody double2 per step
+// (step-major); ring wraps split the copy.
+int copy_history(btdf_ctx* ctx, int32_t body, int64_t first, int64_t n, double2* dst) {
+    const int64_t H = ctx->cfg.history_len;
+    const int nb = (int)ctx->bodies.size();
+    int64_t done = 0;
+    while (done < n) {
+        const int64_t slot = (first + done) % H;
+        const int64_t cnt = std::min<int64_t>(n - done, H - slot);
+        if (body < 0)
+            CK(cudaMemcpyAsync(dst + done * nb, ctx->d_hist + slot * nb, sizeof(double2) * nb * cnt,
+                               cudaMemcpyDeviceToHost, ctx->stream));
+        else
+            CK(cudaMemcpy2DAsync(dst + done, sizeof(double2), ctx->d_hist + slot * nb + body,
+                                 sizeof(double2) * nb, sizeof(double2), (size_t)cnt,
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+        done += cnt;
+    }
+    return BTDF_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -881,12 +924,12 @@ int btdf_create(const btdf_config* cfg, void* stream, btdf_ctx** out) {
         ctx->pf_grid[1] = (long long)sms * collide_stream_blocks_per_sm(c.storage, true, kVarReg2Pf);
         // half a wave of resident warps (measured: 5% faster on 8192 x 4096,
         // no gain on 1600 x 800, where the autotuner keeps variant 9)
-        for (int k = 0; k < 2; k++)
+        const int pfv[3] = {kVarReg2OccPf, kVarReg4L2Pf, kVarPackedL2Pf};
+        for (int k = 0; k < 3; k++)
             for (int pull = 0; pull < 2; pull++)
                 ctx->pf_units[k][pull] =
-                    (long long)sms *
-                    collide_stream_blocks_per_sm(c.storage, pull != 0, k ? kVarReg4L2Pf : kVarReg2OccPf) *
-                    (collide_stream_block_threads(c.storage, k ? kVarReg4L2Pf : kVarReg2OccPf) / 32) / 2;
+                    (long long)sms * collide_stream_blocks_per_sm(c.storage, pull != 0, pfv[k]) *
+                    (collide_stream_block_threads(c.storage, pfv[k]) / 32) / 2;
     }
     const size_t bytes = (size_t)9 * ctx->plane * ctx->elem;
     for (int i = 0; i < 2; i++) {
@@ -986,10 +1029,6 @@ int btdf_add_markers(btdf_ctx* ctx, int32_t n, const double* X, const double* Y,
             return fail(ctx, BTDF_EINVAL, "marker velocity not finite");
     const int rcp = check_positions(ctx, n, X, Y);
     if (rcp != BTDF_OK) return rcp;
-    if (ctx->cfg.bc_x == BTDF_BCX_CONVECTIVE)
-        for (int l = 0; l < n; l++)   // the outlet column's buffer changes while the IB stage runs
-            if ((int)std::floor(X[l] - 0.5 * ctx->width) + ctx->width > ctx->cfg.nx - 2)
-                return fail(ctx, BTDF_EINVAL, "a marker support reaches the convective outlet column");
     Body B;
     B.first = ctx->nmark;
     B.n = n;
@@ -1042,10 +1081,13 @@ int btdf_set_boundary_velocity(btdf_ctx* ctx, const double* ubx, const double* u
 
 int btdf_set_marker_velocity(btdf_ctx* ctx, int32_t body, const double* Ubx, const double* Uby) {
     if (!ctx) return BTDF_EINVAL;
-    if (body < 0 || body >= (int)ctx->bodies.size() || !Ubx || !Uby)
+    if (body < -1 || body >= (int)ctx->bodies.size() || !Ubx || !Uby || ctx->nmark == 0)
         return fail(ctx, BTDF_EINVAL, "bad body index or null velocity");
-    Body& B = ctx->bodies[body];
-    for (int l = 0; l < B.n; l++)
+    // body -1: every body, markers in the order they were added
+    const int b0 = body < 0 ? 0 : body, b1 = body < 0 ? (int)ctx->bodies.size() : body + 1;
+    const int first = ctx->bodies[b0].first;
+    const int count = ctx->bodies[b1 - 1].first + ctx->bodies[b1 - 1].n - first;
+    for (int l = 0; l < count; l++)
         if (!std::isfinite(Ubx[l]) || !std::isfinite(Uby[l]))
             return fail(ctx, BTDF_EINVAL, "marker velocity not finite");
     // this staging slot may still feed an upload kStageSlots calls back
@@ -1053,16 +1095,21 @@ int btdf_set_marker_velocity(btdf_ctx* ctx, int32_t body, const double* Ubx, con
     ctx->aux_slot = (k + 1) % kStageSlots;
     CK(cudaEventSynchronize(ctx->aux_ev[k]));
     MarkerAux* stage = ctx->aux_pin + (size_t)k * ctx->nmark;
-    for (int l = 0; l < B.n; l++) {
-        B.Ubx[l] = Ubx[l];
-        B.Uby[l] = Uby[l];
-        MarkerAux& A = ctx->aux_host[B.first + l];
-        A.ubx_rel = (float)(Ubx[l] - ctx->u_ref * B.wsum[l]);
-        A.uby_rel = (float)Uby[l];
-        stage[B.first + l] = A;
+    for (int b = b0; b < b1; b++) {
+        Body& B = ctx->bodies[b];
+        const double* ux = Ubx + (B.first - first);
+        const double* uy = Uby + (B.first - first);
+        for (int l = 0; l < B.n; l++) {
+            B.Ubx[l] = ux[l];
+            B.Uby[l] = uy[l];
+            MarkerAux& A = ctx->aux_host[B.first + l];
+            A.ubx_rel = (float)(ux[l] - ctx->u_ref * B.wsum[l]);
+            A.uby_rel = (float)uy[l];
+            stage[B.first + l] = A;
+        }
     }
     ctx->tape.pending = false;
-    CK(cudaMemcpyAsync(ctx->d_aux + B.first, stage + B.first, sizeof(MarkerAux) * B.n,
+    CK(cudaMemcpyAsync(ctx->d_aux + first, stage + first, sizeof(MarkerAux) * count,
                        cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaEventRecord(ctx->aux_ev[k], ctx->stream));
     return BTDF_OK;
@@ -1107,13 +1154,14 @@ int64_t btdf_step_count(const btdf_ctx* ctx) { return ctx ? ctx->steps : -1; }
 
 int btdf_read_forces(btdf_ctx* ctx, int32_t body, int64_t first, int64_t n, double* Fx, double* Fy) {
     if (!ctx) return BTDF_EINVAL;
-    if (body < 0 || body >= (int)ctx->bodies.size() || n < 0 || (n > 0 && (!Fx || !Fy)))
+    if (body < -1 || body >= (int)ctx->bodies.size() || ctx->bodies.empty() || n < 0 ||
+        (n > 0 && (!Fx || !Fy)))
         return fail(ctx, BTDF_EINVAL, "bad body index, count or null output");
     const int64_t H = ctx->cfg.history_len;
     if (first < ctx->hist_from || first < ctx->steps - H || first + n > ctx->steps)
         return fail(ctx, BTDF_EINVAL, "requested steps are not in the force history");
-    const int nb = (int)ctx->bodies.size();
-    const size_t need = sizeof(double2) * (size_t)std::max<int64_t>(n, 1);
+    const int64_t nval = n * (body < 0 ? (int64_t)ctx->bodies.size() : 1);
+    const size_t need = sizeof(double2) * (size_t)std::max<int64_t>(nval, 1);
     if (ctx->pin_cap < need) {
         CK(cudaStreamSynchronize(ctx->stream));
         if (ctx->pin) cudaFreeHost(ctx->pin);
@@ -1123,18 +1171,10 @@ int btdf_read_forces(btdf_ctx* ctx, int32_t body, int64_t first, int64_t n, doub
         ctx->pin_cap = need;
     }
     double2* tmp = (double2*)ctx->pin;
-    int64_t done = 0;
-    while (done < n) {
-        const int64_t s = first + done;
-        const int64_t slot = s % H;
-        const int64_t cnt = std::min<int64_t>(n - done, H - slot);
-        CK(cudaMemcpy2DAsync(tmp + done, sizeof(double2), ctx->d_hist + slot * nb + body,
-                             sizeof(double2) * nb, sizeof(double2), (size_t)cnt,
-                             cudaMemcpyDeviceToHost, ctx->stream));
-        done += cnt;
-    }
+    const int rcc = copy_history(ctx, body, first, n, tmp);
+    if (rcc != BTDF_OK) return rcc;
     const int rc = read_status(ctx);   // one synchronization for both copies
-    for (int64_t i = 0; i < n; i++) {
+    for (int64_t i = 0; i < nval; i++) {
         Fx[i] = tmp[i].x;
         Fy[i] = tmp[i].y;
     }
@@ -1143,22 +1183,13 @@ int btdf_read_forces(btdf_ctx* ctx, int32_t body, int64_t first, int64_t n, doub
 
 int btdf_read_forces_async(btdf_ctx* ctx, int32_t body, int64_t first, int64_t n, double* F) {
     if (!ctx) return BTDF_EINVAL;
-    if (body < 0 || body >= (int)ctx->bodies.size() || n < 0 || (n > 0 && !F))
+    if (body < -1 || body >= (int)ctx->bodies.size() || ctx->bodies.empty() || n < 0 ||
+        (n > 0 && !F))
         return fail(ctx, BTDF_EINVAL, "bad body index, count or null output");
     const int64_t H = ctx->cfg.history_len;
     if (first < ctx->hist_from || first < ctx->steps - H || first + n > ctx->steps)
         return fail(ctx, BTDF_EINVAL, "requested steps are not in the force history");
-    const int nb = (int)ctx->bodies.size();
-    int64_t done = 0;
-    while (done < n) {
-        const int64_t slot = (first + done) % H;
-        const int64_t cnt = std::min<int64_t>(n - done, H - slot);
-        CK(cudaMemcpy2DAsync(F + 2 * done, sizeof(double2), ctx->d_hist + slot * nb + body,
-                             sizeof(double2) * nb, sizeof(double2), (size_t)cnt,
-                             cudaMemcpyDeviceToHost, ctx->stream));
-        done += cnt;
-    }
-    return BTDF_OK;
+    return copy_history(ctx, body, first, n, (double2*)F);
 }
 
 int btdf_read_markers(btdf_ctx* ctx, int32_t body, float* Usx, float* Usy, float* Fbx, float* Fby) {
@@ -1218,7 +1249,7 @@ int btdf_save_state(btdf_ctx* ctx, void* dst, size_t cap, size_t* used) {
     btdf_state_size(ctx, &need);
     if (cap < need) return fail(ctx, BTDF_EINVAL, "destination buffer too small");
     StateHeader h{kStateMagic, ctx->cfg.nx, ctx->cfg.ny, ctx->nxp, ctx->cfg.storage,
-                  ctx->poststream ? 1 : 0, ctx->cfg.layout, ctx->steps};
+                  ctx->poststream ? 1 : 0, ctx->cfg.layout, ctx->steps, ctx->u_ref};
     std::memcpy(dst, &h, sizeof(h));
     const size_t ob = outlet_bytes(ctx);
     CK(cudaMemcpyAsync((char*)dst + sizeof(h), ctx->g[ctx->cur], need - sizeof(h) - ob,
@@ -1239,6 +1270,9 @@ int btdf_load_state(btdf_ctx* ctx, const void* src, size_t len) {
     if (h.magic != kStateMagic || h.nx != ctx->cfg.nx || h.ny != ctx->cfg.ny || h.nxp != ctx->nxp ||
         h.storage != ctx->cfg.storage || h.layout != ctx->cfg.layout || h.steps < 0)
         return fail(ctx, BTDF_EINVAL, "checkpoint does not match this context");
+    // the deviations are relative to the writer's reference velocity
+    if (h.u_ref != ctx->u_ref)
+        return fail(ctx, BTDF_EINVAL, "checkpoint was written with another reference velocity");
     const size_t ob = outlet_bytes(ctx);
     CK(cudaMemcpyAsync(ctx->g[ctx->cur], (const char*)src + sizeof(h), need - sizeof(h) - ob,
                        cudaMemcpyHostToDevice, ctx->stream));
@@ -1291,6 +1325,14 @@ int btdf_tune(btdf_ctx* ctx, int32_t variant, int32_t grid_blocks) {
     drop_graphs(ctx);
     ctx->variant = variant;
     ctx->grid_override = grid_blocks;
+    return BTDF_OK;
+}
+
+int btdf_set_wait_limit(btdf_ctx* ctx, int32_t polls) {
+    if (!ctx) return BTDF_EINVAL;
+    CK(cudaStreamSynchronize(ctx->stream));
+    drop_graphs(ctx);   // the graphs hold the old limit in their kernel arguments
+    ctx->wait_polls = polls < 0 ? -1 : polls;
     return BTDF_OK;
 }
 
@@ -1479,6 +1521,8 @@ int btdf_autotune(btdf_ctx* ctx, int32_t steps, int32_t flush_l2, int32_t* chose
         float best_ms = 0.f;
         for (int v = 1; v < kVarCount; v++) {
             if (is_tma(v) && !ctx->tma_ok) continue;
+            // the packed variants run the 4-node kernels with FP32 storage
+            if ((v == kVarPacked || v == kVarPackedL2Pf) && ctx->cfg.storage == kStoreF32) continue;
             ctx->variant = v;
             for (int i = 0; i < 3; i++) {
                 int rc = enqueue_step(ctx, st, true, ctx->cur, false);

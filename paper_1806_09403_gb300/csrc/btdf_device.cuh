@@ -361,6 +361,45 @@ __device__ __forceinline__ void read_node(const T* __restrict__ g, const Lattice
     }
 }
 
+// read_node for the IB stage, which reads one node per lane: the nine source
+// offsets of the pull are formed first (selects, no memory traffic) and the
+// nine loads are then issued back to back, so their latencies overlap instead
+// of queueing behind the stores of an out-of-line call.  The arithmetic is
+// pull_raw's (load plus the bounce-back constant); the inlet and outlet
+// columns and the box's outer nodes keep their own paths.
+template <typename T>
+__device__ __forceinline__ void gather_node(const T* __restrict__ g, const LatticeParams& p, bool pull,
+                                            int x, int y, float f[9]) {
+    if (!pull) {
+        unsigned off[9];
+#pragma unroll
+        for (int a = 0; a < 9; a++) off[a] = p.poff[a] + (unsigned)y * p.rs + (unsigned)x;
+#pragma unroll
+        for (int a = 0; a < 9; a++) f[a] = Io<T>::ld1(g + off[a]);
+        return;
+    }
+    if ((p.box != nullptr && (x == 0 || x == p.nx - 1 || y == 0 || y == p.ny - 1)) ||
+        (p.bcx == kBcxInout && (x == 0 || x == p.nx - 1))) {
+        read_node<T>(g, p, true, x, y, f);
+        return;
+    }
+    unsigned off[9];
+    float add[9];
+#pragma unroll
+    for (int a = 0; a < 9; a++) {
+        int pa, sy, dx;
+        y_source(a, y, p, pa, sy, dx, add[a]);
+        int sx = x + dx;
+        if (sx < 0 || sx >= p.nx) sx = sx < 0 ? sx + p.nx : sx - p.nx;   // periodic x only here
+        off[a] = p.poff[pa] + (unsigned)sy * p.rs + (unsigned)sx;
+    }
+    float v[9];
+#pragma unroll
+    for (int a = 0; a < 9; a++) v[a] = Io<T>::ld1(g + off[a]);
+#pragma unroll
+    for (int a = 0; a < 9; a++) f[a] = v[a] + add[a];
+}
+
 // Lanes per marker: S*S support nodes rounded up to a power of two.
 template <int S> struct Group { static constexpr int G = (S * S <= 4) ? 4 : 16; };
 

@@ -129,6 +129,11 @@ struct LatticeParams {
     // arithmetic of two nodes at once (c1, kr, wom), and 1 - 1/tau.
     float2 c1p[9], krp[9], womp[9];
     float2 omop;
+    // With U_r = (urx, 0) the pairs above take three values each: c1 and k by
+    // e_x (index e_x + 1), w / tau by weight class (rest, axis, diagonal).
+    // The packed 16-bit kernel indexes these, so its 27 constant pairs need
+    // 9 registers' worth instead of 27.
+    float2 c1e[3], kre[3], womw[3];
     float gx, gy;              // uniform body force
     // Convective outlet (null: zero-gradient): the outlet column's
     // post-streaming deviations of the previous step, [9][ny], and the
@@ -148,6 +153,9 @@ struct LatticeParams {
     // ahead (about half a wave of resident warps later; 0: off).
     int pf_ahead;
     int* status;               // sticky device status bits
+    // Polls before a TMA stage wait gives up (< 0: the default bound of about
+    // a second); set by btdf_set_wait_limit to exercise the timeout path.
+    int wait_polls;
     // Force on each body (Eq. 27), reduced in FP64 by block 0 of the LBM kernel.
     int nbody;
     int hist_len;
@@ -212,7 +220,9 @@ enum : int {
     kVarReg2Occ = 9,   // 2 nodes per lane, 5 blocks per SM (<= 48 registers)
     kVarReg2OccPf = 10, // as 9, each warp also prefetches a later row segment into L2
     kVarReg4L2Pf = 11, // as 1, with the L2 prefetch of 10
-    kVarCount = 12
+    kVarPacked = 12,   // 16-bit storage: 8 nodes per lane, planes kept packed (else as 1)
+    kVarPackedL2Pf = 13, // as 12, with the L2 prefetch of 10 (else as 11)
+    kVarCount = 14
 };
 // map: 3-D tensor map (x, y, population) of the input buffer with box
 // (128 + 2 * tma_halo(storage), tma_box_rows(variant), 9).
@@ -228,8 +238,10 @@ cudaError_t launch_ib_force_batch(int storage, bool pull, int width, const void*
                                   const IbParams& q, cudaStream_t st);
 int tma_box_rows(int variant);
 int tma_halo(int storage);
+// pdl: launch as a programmatic dependent of the preceding kernel (the IB
+// kernel loads its marker tables, then waits for that kernel's results).
 cudaError_t launch_ib_force(int storage, bool pull, int width, const void* g,
-                            const LatticeParams& p, const IbParams& q, cudaStream_t st);
+                            const LatticeParams& p, const IbParams& q, bool pdl, cudaStream_t st);
 cudaError_t launch_init_equilibrium(int storage, void* g, const LatticeParams& p,
                                     const double* rho, const double* ux, const double* uy,
                                     cudaStream_t st);

@@ -3,16 +3,19 @@
 //
 // Some callers cannot call cudaMalloc: code running inside another
 // framework's memory budget (a caching allocator that owns every byte of the
-// device), code issued while a CUDA stream is being captured into a graph
-// (where allocation calls are not permitted), or real-time loops that must
-// not enter the driver's allocator.  They bring their own population buffer
-// and output arrays; the per-marker tables and the reduction scratch this
-// stage needs live in one fixed, file-scope device array instead of being
-// allocated.  The arithmetic is the library's own IB kernel.
+// device), or real-time loops that must not enter the driver's allocator.
+// They bring their own population buffer and output arrays; the per-marker
+// tables and the reduction scratch this stage needs live in one fixed,
+// file-scope device array instead of being allocated.  The call copies its
+// host inputs from pageable memory and synchronizes its stream before it
+// returns.  The arithmetic is the library's own IB kernel.
 #include "btdf.h"
 #include "btdf_internal.cuh"
 
+#include <cuda.h>
+
 #include <cmath>
+#include <cstdint>
 #include <mutex>
 
 using namespace btdf;
@@ -37,23 +40,63 @@ constexpr size_t kScratchBytes = (kOffStatus + sizeof(int) + 255) / 256 * 256;
 // Every GPU that loads the library holds this array until the process exits.
 static __device__ __align__(256) unsigned char g_static_scratch[kScratchBytes];
 
+// Device address of the scratch array, looked up once per device and CUDA
+// context with that device current (host code must not use the symbol itself
+// as an address).  The cache is keyed on the context's unique id, so a
+// context created after cudaDeviceReset (which reloads the module) gets a
+// fresh lookup instead of a dangling address.
 std::mutex g_mu;
-void* g_scratch_addr[kMaxDevices] = {};
+struct ScratchSlot {
+    unsigned long long ctx_id;
+    void* addr;
+};
+ScratchSlot g_scratch[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device, looked up once
-// per device with that device current (host code must not use the symbol
-// itself as an address).
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+// Unique id of the current context (0 if none is current yet).
+bool current_context_id(unsigned long long* id) {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    if (!get_current || !get_id) {
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) !=
+                cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) !=
+                cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2) {
+            cudaGetLastError();
+            return false;
+        }
+        get_current = (CtxGetCurrentFn)f1;
+        get_id = (CtxGetIdFn)f2;
+    }
+    CUcontext c = nullptr;
+    if (get_current(&c) != CUDA_SUCCESS) return false;
+    *id = 0;
+    return c == nullptr || get_id(c, id) == CUDA_SUCCESS;
+}
+
 int scratch_address(unsigned char** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return BTDF_ECUDA;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (g_scratch_addr[dev] == nullptr) {
+    unsigned long long id = 0;
+    if (!current_context_id(&id)) return BTDF_ECUDA;
+    if (id == 0 || g_scratch[dev].addr == nullptr || g_scratch[dev].ctx_id != id) {
+        // cudaGetSymbolAddress makes the device's primary context current
+        // if none is; the id is read again afterwards
         void* ptr = nullptr;
         if (cudaGetSymbolAddress(&ptr, g_static_scratch) != cudaSuccess || ptr == nullptr)
             return BTDF_ECUDA;
-        g_scratch_addr[dev] = ptr;
+        if (!current_context_id(&id) || id == 0) return BTDF_ECUDA;
+        g_scratch[dev].ctx_id = id;
+        g_scratch[dev].addr = ptr;
     }
-    *out = (unsigned char*)g_scratch_addr[dev];
+    *out = (unsigned char*)g_scratch[dev].addr;
     return BTDF_OK;
 }
 
@@ -79,7 +122,7 @@ __device__ double delta_eval(int kind, double r) {
 // Marker tables (Eq. 14 weights in FP64, stored as FP32), one thread per
 // marker, built in the scratch array from the positions copied there.
 __global__ void static_tables(const double* in, int n, int kind, int width, int nx, int ny, int px,
-                              int py, double u_in, Marker* mk, MarkerAux* aux) {
+                              int py, double u_ref, Marker* mk, MarkerAux* aux) {
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= n) return;
     const double X = in[l], Y = in[kStaticMaxMarkers + l];
@@ -116,7 +159,7 @@ __global__ void static_tables(const double* in, int n, int kind, int width, int 
     mk[l] = M;
     MarkerAux A;
     A.wsum = (float)wsum;
-    A.ubx_rel = (float)(ubx - u_in * wsum);
+    A.ubx_rel = (float)(ubx - u_ref * wsum);
     A.uby_rel = (float)uby;
     A.body = 0;
     aux[l] = A;
@@ -146,9 +189,9 @@ __global__ void static_force_sum(const float2* F, int n, double2* out) {
 }  // namespace
 
 extern "C" int btdf_ib_forces_static(const btdf_config* cfg, const void* pops, int32_t pull,
-                                     int32_t n, const double* X, const double* Y, const double* Ubx,
-                                     const double* Uby, double ds, double drs, float* Fb,
-                                     double* Fp, void* stream) {
+                                     double u_ref, int32_t n, const double* X, const double* Y,
+                                     const double* Ubx, const double* Uby, double ds, double drs,
+                                     float* Fb, double* Fp, void* stream) {
     if (!cfg || !pops || !X || !Y || !Fb || !Fp) return BTDF_EINVAL;
     const btdf_config& c = *cfg;
     const int width = c.delta == 2 ? 2 : c.delta == 3 ? 3 : (c.delta == 4 || c.delta == 5) ? 4 : 0;
@@ -156,8 +199,13 @@ extern "C" int btdf_ib_forces_static(const btdf_config* cfg, const void* pops, i
     if (width == 0 || c.nx < 4 || c.ny < 4 || c.storage < 0 || c.storage > 2 || c.bc_x < 0 ||
         c.bc_x > 1 || c.bc_y < 0 || c.bc_y > 2 ||
         (c.layout != BTDF_LAYOUT_PLANES && c.layout != BTDF_LAYOUT_ROWS) || !(ds > 0.0) ||
-        !std::isfinite(c.u_in) || !std::isfinite(drs))
+        !std::isfinite(c.u_in) || std::fabs(c.u_in) >= 0.5 || !std::isfinite(u_ref) ||
+        std::fabs(u_ref) >= 0.5 || !std::isfinite(drs))
         return BTDF_EINVAL;
+    // F_b is written and read as 8-byte pairs; populations are read as
+    // elements of the storage type
+    const uintptr_t elem = c.storage == 0 ? 4 : 2;
+    if ((uintptr_t)Fb % 8 != 0 || (uintptr_t)pops % elem != 0) return BTDF_EINVAL;
     const long long nxp = ((long long)c.nx + 31) / 32 * 32;
     if (9ll * nxp * c.ny >= (1ll << 32)) return BTDF_EINVAL;
     const double half = 0.5 * width;
@@ -191,8 +239,8 @@ extern "C" int btdf_ib_forces_static(const btdf_config* cfg, const void* pops, i
         p.poff[a] = c.layout == BTDF_LAYOUT_ROWS ? (unsigned)(a * nxp) : (unsigned)(a * p.plane);
     p.bcx = c.bc_x;
     p.bcy = c.bc_y;
-    p.u_in = (float)c.u_in;
-    p.urx = (float)c.u_in;
+    p.u_in = (float)c.u_in;       // inlet target of the pull
+    p.urx = (float)u_ref;         // reference velocity of the stored deviations
     p.ury = 0.0f;
 
     IbParams q{};
@@ -222,13 +270,13 @@ extern "C" int btdf_ib_forces_static(const btdf_config* cfg, const void* pops, i
                 : cudaMemsetAsync(in + 3 * kStaticMaxMarkers, 0, nb, st);
     if (e == cudaSuccess) {
         static_tables<<<(n + 127) / 128, 128, 0, st>>>(in, n, c.delta, width, c.nx, c.ny, px ? 1 : 0,
-                                                       py ? 1 : 0, c.u_in, (Marker*)(scratch + kOffMk),
+                                                       py ? 1 : 0, u_ref, (Marker*)(scratch + kOffMk),
                                                        (MarkerAux*)(scratch + kOffAux));
         e = cudaGetLastError();
     }
     // the status word keeps the previous call's value: clear it
     if (e == cudaSuccess) e = cudaMemsetAsync(scratch + kOffStatus, 0, sizeof(int), st);
-    if (e == cudaSuccess) e = launch_ib_force(c.storage, pull != 0, width, pops, p, q, st);
+    if (e == cudaSuccess) e = launch_ib_force(c.storage, pull != 0, width, pops, p, q, false, st);
     if (e == cudaSuccess) {
         static_force_sum<<<1, 256, 0, st>>>((const float2*)Fb, n, (double2*)(scratch + kOffSum));
         e = cudaGetLastError();

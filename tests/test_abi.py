@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_1806_09403_gb300 import _build
@@ -104,3 +105,27 @@ def test_batch_rejects_mixed_delta_and_mdf():
     cfgs[1].nf = 2
     assert B.lib().btdf_batch_create(cfgs, 2, None, C.byref(out)) == B.BTDF_EINVAL
     assert B.lib().btdf_batch_create(cfgs, 0, None, C.byref(out)) == B.BTDF_EINVAL
+
+
+@pytest.mark.parametrize("storage,pops,fb", [
+    (0, 16, 4),      # F_b not 8-byte aligned
+    (0, 18, 16),     # FP32 populations not 4-byte aligned
+    (1, 17, 16),     # FP16 populations not 2-byte aligned
+    (2, 33, 64),     # BF16 populations not 2-byte aligned
+])
+def test_static_rejects_misaligned_pointers(storage, pops, fb):
+    """btdf_ib_forces_static refuses misaligned device pointers with EINVAL
+    before any device work (the pointer values here are never dereferenced)."""
+    cfg = B.btdf_config_default()
+    cfg.storage = storage
+    X = np.full(10, 10.0)
+    rc, _ = B.btdf_ib_forces_static(cfg, pops, False, X, X, 1.0, fb_ptr=fb)
+    assert rc == B.BTDF_EINVAL
+
+
+@pytest.mark.parametrize("u_ref", [float("nan"), 0.5, -0.7])
+def test_static_rejects_bad_reference_velocity(u_ref):
+    cfg = B.btdf_config_default()
+    X = np.full(10, 10.0)
+    rc, _ = B.btdf_ib_forces_static(cfg, 16, False, X, X, 1.0, fb_ptr=16, u_ref=u_ref)
+    assert rc == B.BTDF_EINVAL
