@@ -442,8 +442,7 @@ def drag_error(B, case, storage, stream, sim_hist, n):
 
 
 VARIANT_NAMES = {1: "reg4", 2: "reg2", 3: "tma8x2", 4: "tma8x3", 5: "tma16x2", 6: "reg4pf",
-                 7: "reg2pf", 8: "reg1", 9: "reg2o", 10: "reg2o_l2pf", 11: "reg4_l2pf",
-                 12: "packed8", 13: "packed8_l2pf"}
+                 7: "reg2pf", 8: "reg1", 9: "reg2o", 10: "reg2o_l2pf", 11: "reg4_l2pf"}
 
 
 def our_arm(args):
@@ -667,7 +666,7 @@ def main():
                     choices=["bench", "kernel", "batch", "adjoint", "sweep"])
     ap.add_argument("--no-mixed", dest="mixed", action="store_false",
                     help="skip the FP16 / BF16 storage lines of the default bench")
-    ap.add_argument("--variant", type=int, default=0, choices=list(range(14)))
+    ap.add_argument("--variant", type=int, default=0, choices=list(range(12)))
     ap.add_argument("--layout", default="rows", choices=["rows", "planes"])
     args = ap.parse_args()
     if args.warmup < 3:

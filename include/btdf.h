@@ -260,7 +260,7 @@ int btdf_profile_read(btdf_ctx *ctx, double *ms_ib, double *ms_lbm, int64_t *lau
 
 /* Number of collide-stream variants, 0 (automatic) included: the length of
  * btdf_autotune's ms output. */
-#define BTDF_VARIANT_COUNT 14
+#define BTDF_VARIANT_COUNT 12
 
 /* Variant of the fused collide-stream kernel.  Results do not depend on it.
  *   0 automatic (2 for FP32 storage, 1 for FP16 / BF16)
@@ -276,15 +276,10 @@ int btdf_profile_read(btdf_ctx *ctx, double *ms_ib, double *ms_lbm, int64_t *lau
  *  10 as 9, and each warp prefetches into L2 the row segment that a warp
  *     half a wave later will process
  *  11 as 1, with the L2 prefetch of 10
- *  12 16-bit storage: 8 nodes per lane over 256-node row segments, the nine
- *     planes read as 16-byte vectors and kept packed two nodes per word;
- *     segments with boundary rules or forcing take the 4-node path of 1
- *     (FP32 storage: as 1)
- *  13 as 12, with the L2 prefetch of 10 (FP32 storage: as 11)
  * grid_blocks caps the grid, counted in blocks of the variant: 256 threads,
- * or 128 for variant 2 and, with FP16 / BF16 storage, variants 1 and 8-13.
+ * or 128 for variant 2 and, with FP16 / BF16 storage, variants 1 and 8-11.
  * 0 = default:
- * one 32 x NPL-node row segment per warp for variants 1, 2 and 8-13, so the
+ * one 32 x NPL-node row segment per warp for variants 1, 2 and 8-11, so the
  * block scheduler balances the SMs; SM count x resident blocks per SM for
  * the persistent variants 3-7.
  * Synchronizes and drops cached CUDA graphs.

@@ -164,6 +164,9 @@ struct btdf_ctx {
 
     std::vector<Body> bodies;
     int nmark = 0, nband = 0;
+    // All marker data below (tables, forces, diagnostics, body tables,
+    // spreading table, force history) are carved from one device arena.
+    void* d_arena = nullptr;
     Marker* d_mk = nullptr;
     MarkerAux* d_aux = nullptr;
     float2* d_F[2] = {nullptr, nullptr};
@@ -194,7 +197,7 @@ struct btdf_ctx {
 
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     long long pf_grid[2] = {1, 1};                 // software-pipelined kernel [npl 4/2]
-    long long pf_units[3][2] = {};                 // L2 prefetch distance of variants 10, 11, 13 [local/pull]
+    long long pf_units[2][2] = {};                 // L2 prefetch distance of variants 10, 11 [local/pull]
     long long tma_grid[kVarCount] = {};  // persistent grid of each TMA variant
     int variant = kVarAuto;              // LBM kernel variant (btdf_tune)
     int grid_override = 0;               // 0: SMs x resident blocks
@@ -268,19 +271,30 @@ void free_markers(btdf_ctx* ctx) {
     ctx->aux_pin = nullptr;
     ctx->dev_bytes -= ctx->marker_bytes;
     ctx->marker_bytes = 0;
-    dfree(ctx, ctx->d_mk);
-    dfree(ctx, ctx->d_aux);
-    dfree(ctx, ctx->d_F[0]);
-    dfree(ctx, ctx->d_F[1]);
-    dfree(ctx, ctx->d_Us);
-    dfree(ctx, ctx->d_rhol);
-    dfree(ctx, ctx->d_seg_index);
-    dfree(ctx, ctx->d_seg_ptr);
-    dfree(ctx, ctx->d_csr);
-    dfree(ctx, ctx->d_body_ptr);
-    dfree(ctx, ctx->d_body_scale);
-    dfree(ctx, ctx->d_hist);
+    dfree(ctx, ctx->d_arena);
+    ctx->d_mk = nullptr;
+    ctx->d_aux = nullptr;
+    ctx->d_F[0] = ctx->d_F[1] = nullptr;
+    ctx->d_Us = nullptr;
+    ctx->d_rhol = nullptr;
+    ctx->d_seg_index = nullptr;
+    ctx->d_seg_ptr = nullptr;
+    ctx->d_csr = nullptr;
+    ctx->d_body_ptr = nullptr;
+    ctx->d_body_scale = nullptr;
+    ctx->d_hist = nullptr;
 }
+
+// Sub-buffers of one device allocation, each 256-byte aligned.
+struct Arena {
+    size_t size = 0;
+    template <typename P>
+    size_t take(size_t bytes) {
+        const size_t off = size;
+        size = (size + bytes + 255) / 256 * 256;
+        return off;
+    }
+};
 
 void free_tape(btdf_ctx* ctx) {
     AdjointTape& T = ctx->tape;
@@ -348,11 +362,6 @@ LatticeParams lattice_params(const btdf_ctx* ctx) {
             p.womp[a] = make_float2(p.wom[a], p.wom[a]);
         }
         p.omop = make_float2(p.one_m_omega, p.one_m_omega);
-        for (int a = 0; a < 9; a++) {   // the class tables of the packed kernel
-            p.c1e[ex(a) + 1] = p.c1p[a];
-            p.kre[ex(a) + 1] = p.krp[a];
-            p.womw[a == 0 ? 0 : (a < 5 ? 1 : 2)] = p.womp[a];
-        }
     }
     p.nwork = (long long)ctx->cfg.ny * ctx->nseg;
     // planar: [9][ny][nxp]; row-interleaved: [ny][9][nxp]
@@ -443,8 +452,8 @@ int enqueue_step(btdf_ctx* ctx, cudaStream_t st, bool pull, int cur, bool prof) 
                          : pf                   ? (int)ctx->pf_grid[v == kVarReg2Pf ? 1 : 0]
                                                 : kFullGrid;
         LatticeParams q = p;
-        if (v == kVarReg2OccPf || v == kVarReg4L2Pf || v == kVarPackedL2Pf)
-            q.pf_ahead = (int)ctx->pf_units[v == kVarReg2OccPf ? 0 : v == kVarReg4L2Pf ? 1 : 2][pull ? 1 : 0];
+        if (v == kVarReg2OccPf || v == kVarReg4L2Pf)
+            q.pf_ahead = (int)ctx->pf_units[v == kVarReg4L2Pf ? 1 : 0][pull ? 1 : 0];
         CK(launch_collide_stream(ctx->cfg.storage, pull, v, ctx->g[cur], ctx->g[1 - cur], q, grid, pdl, st));
     }
     if (prof) CK(cudaEventRecord(e2, st));
@@ -557,18 +566,37 @@ int rebuild_markers(btdf_ctx* ctx) {
     const std::vector<CsrEntry>& csr = t.csr;
     const size_t nseg_all = (size_t)ny * ctx->nseg;
     const size_t bytes_before = ctx->dev_bytes;
-    CK(dalloc(ctx, &ctx->d_mk, sizeof(Marker) * nm));
-    CK(dalloc(ctx, &ctx->d_aux, sizeof(MarkerAux) * nm));
-    CK(dalloc(ctx, &ctx->d_F[0], sizeof(float2) * nm));
-    CK(dalloc(ctx, &ctx->d_F[1], sizeof(float2) * nm));
-    CK(dalloc(ctx, &ctx->d_Us, sizeof(float2) * nm));
-    CK(dalloc(ctx, &ctx->d_rhol, sizeof(float) * nm));
-    CK(dalloc(ctx, &ctx->d_seg_index, sizeof(int) * nseg_all));
-    CK(dalloc(ctx, &ctx->d_seg_ptr, sizeof(int) * std::max<size_t>(seg_ptr.size(), 1)));
-    CK(dalloc(ctx, &ctx->d_csr, sizeof(CsrEntry) * std::max<size_t>(csr.size(), 1)));
-    CK(dalloc(ctx, &ctx->d_body_ptr, sizeof(int) * (nb + 1)));
-    CK(dalloc(ctx, &ctx->d_body_scale, sizeof(double) * nb));
-    CK(dalloc(ctx, &ctx->d_hist, sizeof(double2) * (size_t)ctx->cfg.history_len * nb));
+    // One allocation: the tables every IB launch and the body-force
+    // reduction touch come first, so a step's small reads and writes fall
+    // in one or two pages (one address translation each) instead of a
+    // dozen separate allocations; the spreading table and the history follow.
+    Arena A;
+    const size_t o_mk = A.take<Marker>(sizeof(Marker) * nm);
+    const size_t o_aux = A.take<MarkerAux>(sizeof(MarkerAux) * nm);
+    const size_t o_F0 = A.take<float2>(sizeof(float2) * nm);
+    const size_t o_F1 = A.take<float2>(sizeof(float2) * nm);
+    const size_t o_Us = A.take<float2>(sizeof(float2) * nm);
+    const size_t o_rhol = A.take<float>(sizeof(float) * nm);
+    const size_t o_bptr = A.take<int>(sizeof(int) * (nb + 1));
+    const size_t o_bsc = A.take<double>(sizeof(double) * nb);
+    const size_t o_segi = A.take<int>(sizeof(int) * nseg_all);
+    const size_t o_segp = A.take<int>(sizeof(int) * std::max<size_t>(seg_ptr.size(), 1));
+    const size_t o_csr = A.take<CsrEntry>(sizeof(CsrEntry) * std::max<size_t>(csr.size(), 1));
+    const size_t o_hist = A.take<double2>(sizeof(double2) * (size_t)ctx->cfg.history_len * nb);
+    CK(dalloc(ctx, &ctx->d_arena, A.size));
+    char* base = (char*)ctx->d_arena;
+    ctx->d_mk = (Marker*)(base + o_mk);
+    ctx->d_aux = (MarkerAux*)(base + o_aux);
+    ctx->d_F[0] = (float2*)(base + o_F0);
+    ctx->d_F[1] = (float2*)(base + o_F1);
+    ctx->d_Us = (float2*)(base + o_Us);
+    ctx->d_rhol = (float*)(base + o_rhol);
+    ctx->d_body_ptr = (int*)(base + o_bptr);
+    ctx->d_body_scale = (double*)(base + o_bsc);
+    ctx->d_seg_index = (int*)(base + o_segi);
+    ctx->d_seg_ptr = (int*)(base + o_segp);
+    ctx->d_csr = (CsrEntry*)(base + o_csr);
+    ctx->d_hist = (double2*)(base + o_hist);
     cudaStream_t st = ctx->stream;
     CK(cudaMemcpyAsync(ctx->d_mk, mk.data(), sizeof(Marker) * nm, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(ctx->d_aux, ctx->aux_host.data(), sizeof(MarkerAux) * nm,
@@ -924,8 +952,8 @@ int btdf_create(const btdf_config* cfg, void* stream, btdf_ctx** out) {
         ctx->pf_grid[1] = (long long)sms * collide_stream_blocks_per_sm(c.storage, true, kVarReg2Pf);
         // half a wave of resident warps (measured: 5% faster on 8192 x 4096,
         // no gain on 1600 x 800, where the autotuner keeps variant 9)
-        const int pfv[3] = {kVarReg2OccPf, kVarReg4L2Pf, kVarPackedL2Pf};
-        for (int k = 0; k < 3; k++)
+        const int pfv[2] = {kVarReg2OccPf, kVarReg4L2Pf};
+        for (int k = 0; k < 2; k++)
             for (int pull = 0; pull < 2; pull++)
                 ctx->pf_units[k][pull] =
                     (long long)sms * collide_stream_blocks_per_sm(c.storage, pull != 0, pfv[k]) *
@@ -1521,8 +1549,6 @@ int btdf_autotune(btdf_ctx* ctx, int32_t steps, int32_t flush_l2, int32_t* chose
         float best_ms = 0.f;
         for (int v = 1; v < kVarCount; v++) {
             if (is_tma(v) && !ctx->tma_ok) continue;
-            // the packed variants run the 4-node kernels with FP32 storage
-            if ((v == kVarPacked || v == kVarPackedL2Pf) && ctx->cfg.storage == kStoreF32) continue;
             ctx->variant = v;
             for (int i = 0; i < 3; i++) {
                 int rc = enqueue_step(ctx, st, true, ctx->cur, false);

@@ -129,11 +129,6 @@ struct LatticeParams {
     // arithmetic of two nodes at once (c1, kr, wom), and 1 - 1/tau.
     float2 c1p[9], krp[9], womp[9];
     float2 omop;
-    // With U_r = (urx, 0) the pairs above take three values each: c1 and k by
-    // e_x (index e_x + 1), w / tau by weight class (rest, axis, diagonal).
-    // The packed 16-bit kernel indexes these, so its 27 constant pairs need
-    // 9 registers' worth instead of 27.
-    float2 c1e[3], kre[3], womw[3];
     float gx, gy;              // uniform body force
     // Convective outlet (null: zero-gradient): the outlet column's
     // post-streaming deviations of the previous step, [9][ny], and the
@@ -220,9 +215,7 @@ enum : int {
     kVarReg2Occ = 9,   // 2 nodes per lane, 5 blocks per SM (<= 48 registers)
     kVarReg2OccPf = 10, // as 9, each warp also prefetches a later row segment into L2
     kVarReg4L2Pf = 11, // as 1, with the L2 prefetch of 10
-    kVarPacked = 12,   // 16-bit storage: 8 nodes per lane, planes kept packed (else as 1)
-    kVarPackedL2Pf = 13, // as 12, with the L2 prefetch of 10 (else as 11)
-    kVarCount = 14
+    kVarCount = 12
 };
 // map: 3-D tensor map (x, y, population) of the input buffer with box
 // (128 + 2 * tma_halo(storage), tma_box_rows(variant), 9).

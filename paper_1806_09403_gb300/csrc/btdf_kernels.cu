@@ -438,170 +438,6 @@ collide_stream_kernel(const T* __restrict__ gin, T* __restrict__ gout, LatticePa
     if (blockIdx.x == 0) body_forces_and_step(p);
 }
 
-// ---- the packed 16-bit LBM kernel ----------------------------------------------
-
-// Stored-scale conversion of one 32-bit word (two nodes) of a 16-bit format.
-template <typename T> struct Pk;
-template <> struct Pk<__half> {
-    static __device__ __forceinline__ float2 to2(unsigned u) { return Raw<__half>::to2(u); }
-    static __device__ __forceinline__ unsigned from2(float2 v) { return Raw<__half>::from2(v.x, v.y); }
-};
-template <> struct Pk<__nv_bfloat16> {
-    using C = Io16<__nv_bfloat16, __nv_bfloat162>;
-    static __device__ __forceinline__ float2 to2(unsigned u) { return C::to2(u); }
-    static __device__ __forceinline__ unsigned from2(float2 v) { return C::from2(v.x, v.y); }
-};
-
-// High half of a, low half of b: the word of the two nodes that straddle the
-// boundary between consecutive words a, b.
-__device__ __forceinline__ unsigned straddle(unsigned a, unsigned b) { return __byte_perm(a, b, 0x5432); }
-
-// One interior row segment of 256 nodes, 8 per lane, with 16-bit storage and
-// neither IB force nor body force on it.  The nine planes are read as
-// 16-byte vectors and stay packed, two nodes per 32-bit word (9 x 4 words per
-// lane).  The streaming shift of a plane moves halves between words with byte
-// permutes; the one half that crosses a lane boundary comes by shuffle and
-// lane 0 / lane 31 fetch theirs from the neighbouring segment.  Node pairs
-// are then unpacked, collided with the same sequence of packed FP32x2
-// operations as collide_store's unforced path (so the results are bitwise
-// those of the 4-node kernels), packed back in place and stored as 16-byte
-// vectors.  Twice the nodes per lane of the 4-node kernels halves the load,
-// store and address instructions per node and doubles the bytes each warp
-// has in flight, at the same register count.
-template <typename T>
-__device__ __forceinline__ void lbm_segment_packed(const T* __restrict__ gin, T* __restrict__ gout,
-                                                   const LatticeParams& p, int y, int xw, int lane) {
-    constexpr float s = 1.0f / Raw<T>::kScale;
-    const int x0 = xw + 8 * lane;
-    const bool live = x0 < p.nxp;
-    const int x0c = live ? x0 : p.nxp - 8;
-    const unsigned rowc = (unsigned)y * p.rs + (unsigned)x0c;
-    unsigned w[9][4];
-#pragma unroll
-    for (int a = 0; a < 9; a++) {
-        const int dx = -ex(a);
-        const unsigned off = p.poff[a] + rowc + (unsigned)(-ey(a) * (int)p.rs);
-        const uint4 v = *reinterpret_cast<const uint4*>(gin + off);
-        w[a][0] = v.x;
-        w[a][1] = v.y;
-        w[a][2] = v.z;
-        w[a][3] = v.w;
-        unsigned edge = 0u;
-        const unsigned short* h = reinterpret_cast<const unsigned short*>(gin);
-        if (dx < 0 && lane == 0 && x0 > 0) edge = (unsigned)h[off - 1] << 16;
-        if (dx > 0 && lane == 31 && x0 + 8 < p.nxp) edge = (unsigned)h[off + 8];
-        if (dx < 0) {           // node i takes node i - 1
-            unsigned prev = __shfl_up_sync(kFull, w[a][3], 1);
-            if (lane == 0) prev = edge;
-            w[a][3] = straddle(w[a][2], w[a][3]);
-            w[a][2] = straddle(w[a][1], w[a][2]);
-            w[a][1] = straddle(w[a][0], w[a][1]);
-            w[a][0] = straddle(prev, w[a][0]);
-        } else if (dx > 0) {    // node i takes node i + 1
-            unsigned next = __shfl_down_sync(kFull, w[a][0], 1);
-            if (lane == 31) next = edge;
-            w[a][0] = straddle(w[a][0], w[a][1]);
-            w[a][1] = straddle(w[a][1], w[a][2]);
-            w[a][2] = straddle(w[a][2], w[a][3]);
-            w[a][3] = straddle(w[a][3], next);
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < 4; j++) {
-        if (j > 0) {
-            // Keep the pairs in sequence: pair j's words are made to depend
-            // (through empty asm, no instruction) on pair j-1's last result,
-            // so the compiler cannot unpack all pairs at once and run out of
-            // registers.
-#pragma unroll
-            for (int a = 0; a < 9; a++) asm volatile("" : "+r"(w[a][j]) : "r"(w[8][j - 1]));
-        }
-        float2 d[9];
-#pragma unroll
-        for (int a = 0; a < 9; a++) d[a] = Pk<T>::to2(w[a][j]);
-        // Moments (Eqs. 9-10) and the collision (Eqs. 5-7) of nodes 2j, 2j+1
-        const Moments2 m = moments2(d, p.urx, p.ury, s);
-        const float2 U = m.dux, V = m.duy;
-        const float2 nU = mul2(U, f2(-1.0f)), nV = mul2(V, f2(-1.0f));
-        float2 t = fma2(U, U, mul2(V, V));
-        t = fma2(f2(2.0f * p.urx), U, t);
-        t = fma2(f2(2.0f * p.ury), V, t);
-        const float2 P = mul2(f2(-1.5f), t);
-#pragma unroll
-        for (int a = 0; a < 9; a++) {
-            // the same constants as c1p[a], krp[a], womp[a] (U_r = (urx, 0))
-            const int ce = ex(a) + 1, cw = a == 0 ? 0 : (a < 5 ? 1 : 2);
-            const float2 ed = edot2(a, U, V, nU, nV);
-            const float2 pdiff = fma2(ed, fma2(f2(4.5f), ed, p.c1e[ce]), P);
-            const float2 deqw = fma2(m.rho, pdiff, mul2(p.kre[ce], m.drho));
-            w[a][j] = Pk<T>::from2(fma2(p.womw[cw], deqw, mul2(p.omop, d[a])));
-        }
-    }
-    if (live && x0 < p.nx) {
-        T* const out = gout + (unsigned)y * p.rs + (unsigned)x0;
-#pragma unroll
-        for (int a = 0; a < 9; a++)
-            *reinterpret_cast<uint4*>(out + p.poff[a]) = make_uint4(w[a][0], w[a][1], w[a][2], w[a][3]);
-    }
-}
-
-// Pull kernel of the 16-bit formats over 256-node row segments (one per warp
-// by default): segments of interior rows that carry neither IB nor body
-// force and contain neither row end take lbm_segment_packed; every other
-// segment (wall and wrap rows, row ends, band segments, the prescribed-velocity
-// box) is processed as two 128-node segments by the 4-node path, which
-// carries every boundary rule and the forcing.
-template <typename T, int MINB>
-__global__ void __launch_bounds__(128, MINB)
-collide_stream_packed_kernel(const T* __restrict__ gin, T* __restrict__ gout, LatticeParams p) {
-    cudaTriggerProgrammaticLaunchCompletion();   // as in collide_stream_kernel
-    constexpr int SW = 256;
-    const int lane = threadIdx.x & 31;
-    const int nsegw = (p.nxp + SW - 1) / SW;
-    const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int y0 = (int)((__umulhi((unsigned)w0, p.wmul) + (unsigned)w0) >> p.wshift);
-    const int s0 = w0 - y0 * nsegw;
-    if (p.pf_ahead > 0) {
-        const int u2 = w0 + p.pf_ahead;
-        if (u2 < (int)p.nwork) {
-            const int y2 = (int)((__umulhi((unsigned)u2, p.wmul) + (unsigned)u2) >> p.wshift);
-            const int x2 = (u2 - y2 * nsegw) * SW;
-            constexpr int LE = 128 / (int)sizeof(T);            // elements per 128-byte line
-            constexpr int LINES = SW / LE;
-            for (int k = lane; k < 9 * LINES; k += 32) {
-                const int a = k / LINES, xl = x2 + (k - a * LINES) * LE;
-                if (xl < p.nxp) {
-                    const T* addr = gin + p.poff[a] + (unsigned)y2 * p.rs + (unsigned)xl;
-                    asm volatile("prefetch.global.L2 [%0];" ::"l"(addr));
-                }
-            }
-        }
-    }
-    const bool plain = p.box == nullptr && p.gx == 0.f && p.gy == 0.f && p.ury == 0.f;
-    int y = y0, s = s0;
-    while (y < p.ny) {
-        const int xw = s * SW;
-        const int segA = band_segment(p, y, xw);
-        const int segB = xw + kSeg < p.nxp ? band_segment(p, y, xw + kSeg) : -1;
-        if (plain && y > 0 && y < p.ny - 1 && xw > 0 && xw + SW < p.nx && segA < 0 && segB < 0) {
-            lbm_segment_packed<T>(gin, gout, p, y, xw, lane);
-        } else {
-#pragma unroll 1
-            for (int hlf = 0; hlf < 2; hlf++) {
-                const int xh = xw + hlf * kSeg;
-                if (xh < p.nxp) lbm_segment<T, true, 4>(gin, gout, p, y, xh, lane, hlf ? segB : segA);
-            }
-        }
-        s += p.wds;
-        y += p.wdy;
-        if (s >= nsegw) {
-            s -= nsegw;
-            y += 1;
-        }
-    }
-    if (blockIdx.x == 0) body_forces_and_step(p);
-}
-
 // ---- the software-pipelined LBM kernel ------------------------------------------
 
 // Raw loads of one interior row segment: the nine vectors and the one value
@@ -1203,28 +1039,6 @@ cudaError_t collide_stream_tn(bool pull, const void* gin, void* gout, LatticePar
     return cudaLaunchKernelEx(&cfg, collide_stream_kernel<T, false, NPL, MB>, a, b, p);
 }
 
-template <typename T, int MB>
-cudaError_t collide_stream_packed_tn(const void* gin, void* gout, LatticeParams p, int grid, bool pdl,
-                                     cudaStream_t st) {
-    constexpr int SW = 256;
-    constexpr int BT = 128;
-    const int nsegw = (p.nxp + SW - 1) / SW;
-    p.nwork = (long long)p.ny * nsegw;
-    const long long need = (p.nwork * 32 + BT - 1) / BT;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)std::min<long long>(need, (long long)grid));
-    cfg.blockDim = dim3(BT);
-    const long long nw = (long long)cfg.gridDim.x * (BT / 32);
-    set_warp_map(p, nsegw, nw);
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = pdl ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, collide_stream_packed_kernel<T, MB>, (const T*)gin, (T*)gout, p);
-}
-
 template <typename T, int NPL>
 cudaError_t collide_stream_pf_tn(const void* gin, void* gout, LatticeParams p, int grid, bool pdl,
                                  cudaStream_t st) {
@@ -1269,12 +1083,6 @@ cudaError_t collide_stream_t(bool pull, int variant, const void* gin, void* gout
     case kVarReg2Occ:
     case kVarReg2OccPf: return collide_stream_tn<T, 2, 5>(pull, gin, gout, p, grid, pdl, st);
     case kVarReg4L2Pf: return collide_stream_tn<T, 4, 3>(pull, gin, gout, p, grid, pdl, st);
-    case kVarPacked:
-    case kVarPackedL2Pf:
-        // 16-bit storage, pull steps; otherwise the 4-node kernel
-        if constexpr (sizeof(T) == 2)
-            if (pull) return collide_stream_packed_tn<T, 6>(gin, gout, p, grid, pdl, st);
-        return collide_stream_tn<T, 4, 3>(pull, gin, gout, p, grid, pdl, st);
     default: return collide_stream_tn<T, 4, 3>(pull, gin, gout, p, grid, pdl, st);
     }
 }
@@ -1301,15 +1109,6 @@ int blocks_per_sm_t(bool pull, int variant) {
     case kVarReg2Occ:
     case kVarReg2OccPf: return blocks_per_sm_tn<T, 2, 5>(pull);
     case kVarReg4L2Pf: return blocks_per_sm_tn<T, 4, 3>(pull);
-    case kVarPacked:
-    case kVarPackedL2Pf:
-        if constexpr (sizeof(T) == 2)
-            if (pull) {
-                int n = 0;
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, collide_stream_packed_kernel<T, 6>, 128, 0);
-                return n > 0 ? n : 1;
-            }
-        return blocks_per_sm_tn<T, 4, 3>(pull);
     default: return blocks_per_sm_tn<T, 4, 3>(pull);
     }
 }
@@ -1530,8 +1329,6 @@ int collide_stream_block_threads(int storage, int variant) {
     case kVarReg1: return lbm_block_threads(eb, 1, 6);
     case kVarReg2Occ:
     case kVarReg2OccPf: return lbm_block_threads(eb, 2, 5);
-    case kVarPacked:
-    case kVarPackedL2Pf: return 128;
     default: return lbm_block_threads(eb, 4, 3);
     }
 }
