@@ -7,7 +7,11 @@ each, 25,200 markers) at seeded non-overlapping centres, Re = 200
 drs = 1.9, FP32 arithmetic with FP32 deviation storage.  One step = the IB
 stage plus the fused collide-stream kernel.  The same lattice is then timed
 with FP16 and BF16 storage (mixed_precision), and the drag of every body over
-the oracle's sample is compared with the FP64 oracle (cd_err_vs_fp64).
+the oracle's sample is compared with the FP64 oracle (cd_err_vs_fp64).  On one
+GPU the line also carries the batched form (512 uneven single-cylinder
+lattices in one launch per step against the same cases one at a time) and
+the adjoint window (forward and reverse sweep on the 800 x 400 cylinder);
+--no-extras leaves them out.
 --workload paper selects the 1600 x 800 cylinder (Sec. 5.2 geometry, whose
 92 MB of populations fit in L2); --mode sweep runs that cylinder over the
 Re x delta grid.
@@ -253,33 +257,29 @@ def kernel_mode(args):
     return 0
 
 
-def batch_mode(args):
+def measure_batch(B, args, stream, steps):
     """512 independent single-cylinder cases of uneven sizes in one batched
-    launch per step, against the same cases run one at a time."""
+    launch per step (library autotuner picks the launch shape), against the
+    same cases run one at a time, each in its own context through CUDA
+    graphs.  Returns a dict of the measurements."""
     import torch
-    torch.cuda.set_device(0)
-    import __graft_entry__
-    __graft_entry__.build()
     import workloads as W
-    from paper_1806_09403_gb300 import btdf as B
     cases = W.batch_cases(512, seed=7)
     nodes = sum(c.nx * c.ny for c in cases)
-    stream = torch.cuda.current_stream()
     storage = {"f32": 0, "f16": 1, "bf16": 2}[args.storage]
     bt = B.Batch.from_cases(cases, storage=storage, history_len=64, stream=stream.cuda_stream)
-    bt.step(args.warmup)
+    bt.step(max(args.warmup, 3))
     bt.sync()
-    # launch shape picked by the library's autotuner on the batch itself
     best, tune = bt.autotune(16, False)
     bt.step(32)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    bt.step(args.steps)
+    bt.step(steps)
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    value = nodes * args.steps / (ms / 1e3) / 1e6
+    value = nodes * steps / (ms / 1e3) / 1e6
     unstable = 0
     body = 0
     for c in cases:
@@ -287,8 +287,7 @@ def batch_mode(args):
         unstable += int(not np.isfinite(fx[0]))
         body += len(c.bodies)
     bt.close()
-    # the same cases one at a time: each its own context, stepped through graphs
-    k1 = min(args.steps, 200)
+    k1 = min(steps, 200)
     tot = 0.0
     for c in cases:
         lat = B.Lattice.from_case(c, storage=storage, stream=stream.cuda_stream, history_len=64)
@@ -298,40 +297,50 @@ def batch_mode(args):
         lat.step(k1)
         b.record(stream)
         torch.cuda.synchronize()
-        tot += a.elapsed_time(b) / k1 * args.steps
+        tot += a.elapsed_time(b) / k1 * steps
         lat.close()
-    one = nodes * args.steps / (tot / 1e3) / 1e6
+    one = nodes * steps / (tot / 1e3) / 1e6
+    return {"value": value, "unit": "MLUPS", "steps": steps, "ms_per_step": ms / steps,
+            "nodes": nodes, "l2": "inputs (%.1f GB) larger than L2" % (nodes * 72 / 1e9),
+            "one_at_a_time_mlups": one, "speedup_vs_one_at_a_time": value / one,
+            "launch_variant": {"chosen": best, "ms_per_step": tune}, "unstable_cases": unstable,
+            "workload": "512 single-cylinder cases, nx in 128..1024, ny = nx/2, D in "
+                        "[10, min(40, ny/5)], Re in {0.1, 40, 200}, 3-point delta, graph replay"}
+
+
+def batch_mode(args):
+    """The batched form on its own (see measure_batch)."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1806_09403_gb300 import btdf as B
+    storage = {"f32": 0, "f16": 1, "bf16": 2}[args.storage]
+    m = measure_batch(B, args, torch.cuda.current_stream(), args.steps)
     print(json.dumps({
-        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "metric": METRIC, "value": m["value"], "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": {0: "f32", 1: "f32 (f16 storage)",
                                                          2: "f32 (bf16 storage)"}[storage],
         "data": "synthetic",
-        "config": {"workload": "batch of 512 single-cylinder cases, nx in 128..1024, ny = nx/2, "
-                               "D in [10, min(40, ny/5)], Re in {0.1, 40, 200}, 3-point delta",
-                   "nodes": nodes, "storage": args.storage,
-                   "l2": "inputs (%.1f GB) larger than L2" % (nodes * 72 / 1e9)},
-        "one_at_a_time_mlups": one, "speedup_vs_one_at_a_time": value / one,
-        "launch_variant": {"chosen": best, "ms_per_step": tune},
-        "unstable_cases": unstable,
+        "config": {"workload": m["workload"], "nodes": m["nodes"], "storage": args.storage,
+                   "l2": m["l2"]},
+        "one_at_a_time_mlups": m["one_at_a_time_mlups"],
+        "speedup_vs_one_at_a_time": m["speedup_vs_one_at_a_time"],
+        "launch_variant": m["launch_variant"], "unstable_cases": m["unstable_cases"],
         "gpu_launches": 2 * args.steps,
     }))
     return 0
 
 
-def adjoint_mode(args):
+def measure_adjoint(B, stream, reps):
     """Adjoint window on the 800 x 400 cylinder (D = 24, 76 markers, Re = 100,
     3-point delta): 500 steps after a 2000-step spin-up, a checkpoint every
     50 steps.  Times the forward window (J) and the reverse sweep (dJ/dU and
     dJ/dX, dJ/dY of every marker) through the C ABI."""
     import torch
-    torch.cuda.set_device(0)
-    import __graft_entry__
-    __graft_entry__.build()
     import workloads as W
-    from paper_1806_09403_gb300 import btdf as B
     case = W.adjoint_cylinder()
-    stream = torch.cuda.current_stream()
     lat = B.Lattice.from_case(case, stream=stream.cuda_stream, history_len=1024)
     lat.step(2000)
     lat.sync()
@@ -339,7 +348,6 @@ def adjoint_mode(args):
     nodes = case.nx * case.ny
     lat.adjoint_forward(nsteps, every, 0, case.D)   # warm-up (allocates the tape)
     lat.adjoint_backward()
-    reps = max(1, min(args.steps, 20))
     tf = tb = 0.0
     for _ in range(reps):
         torch.cuda.synchronize()
@@ -353,9 +361,9 @@ def adjoint_mode(args):
     tf /= reps
     tb /= reps
     nm = len(case.bodies[0].X)
-    print(json.dumps({
-        "mode": "adjoint", "workload": "cylinder 800x400, D=24, 76 markers, Re=100 (tau=0.536), "
-                                      "3-point delta; window of 500 steps, checkpoint every 50",
+    out = {
+        "workload": "cylinder 800x400, D=24, 76 markers, Re=100 (tau=0.536), 3-point delta; "
+                    "window of 500 steps, checkpoint every 50",
         "J": J, "dJdU": dU, "reps": reps,
         "forward_ms": tf * 1e3, "backward_ms": tb * 1e3,
         "forward_mlups": nodes * nsteps / tf / 1e6,
@@ -364,7 +372,21 @@ def adjoint_mode(args):
         "gradient_entries": 1 + 2 * nm,
         "central_fd_cost_over_adjoint": 2 * (1 + nm) * tf / (tf + tb),
         "tape_device_mb": lat.device_bytes() / 1e6,
-    }))
+    }
+    lat.close()
+    return out
+
+
+def adjoint_mode(args):
+    """The adjoint window on its own (see measure_adjoint)."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1806_09403_gb300 import btdf as B
+    out = measure_adjoint(B, torch.cuda.current_stream(), max(1, min(args.steps, 20)))
+    out["mode"] = "adjoint"
+    print(json.dumps(out))
     return 0
 
 
@@ -540,6 +562,12 @@ def our_arm(args):
             mm["traffic"] = ncu_traffic(args.workload, st)
             mixed[name] = mm
 
+    # ---- the batched and the differentiated forms (one GPU, rank 0) ----
+    batch = adjoint = None
+    if rank == 0 and world == 1 and args.extras:
+        batch = measure_batch(B, args, stream, 200)
+        adjoint = measure_adjoint(B, stream, 3)
+
     # ---- FP64 oracle on the host cores, and drag error against it ----
     cpu = None
     cd_err = {}
@@ -604,6 +632,8 @@ def our_arm(args):
                                 "traffic": v["traffic"], "bytes_per_lu": 36,
                                 "variant": v["variant"], "speedup_vs_f32": v["value"] / value}
                             for k, v in mixed.items()} or None,
+        "batch": batch,
+        "adjoint": adjoint,
     }
     print(json.dumps(line))
     return 0
@@ -637,10 +667,18 @@ def sweep_mode(args):
     for re_ in (0.1, 40.0, 200.0):
         for delta in (2, 3, 4):
             case = W.paper_cylinder(re=re_, delta=delta)
-            lat, m = measure_storage(B, case, storage, args, stream, 1, flush_l2, barrier, layout,
-                                     max(args.steps + args.warmup + 64, 4096), tune_steps=16)
+            # The 2-point function diverges at Re >= 40 (within about 50 steps
+            # at Re = 200): time its stable stretch only, with variant 11 and
+            # no autotuning (3 + 3 x 8 steps).
+            unstable = delta == 2 and re_ >= 40.0
+            a = argparse.Namespace(**vars(args))
+            if unstable:
+                a.steps, a.warmup, a.variant = min(args.steps, 8), 3, 11
+            lat, m = measure_storage(B, case, storage, a, stream, 1, flush_l2, barrier, layout,
+                                     max(a.steps + a.warmup + 64, 4096), tune_steps=16)
             lat.close()
             points.append({"re": re_, "delta": delta, "tau": case.tau, "mlups": m["value"],
+                           "steps": a.steps, "stable_stretch_only": unstable,
                            "ms_per_step_median": m["ms_per_step_median"],
                            "kernel_ms_per_launch": m["kernel_ms_per_launch"],
                            "ib_ms_per_step": m["ib_ms_per_step"],
@@ -666,6 +704,8 @@ def main():
                     choices=["bench", "kernel", "batch", "adjoint", "sweep"])
     ap.add_argument("--no-mixed", dest="mixed", action="store_false",
                     help="skip the FP16 / BF16 storage lines of the default bench")
+    ap.add_argument("--no-extras", dest="extras", action="store_false",
+                    help="skip the batched-form and adjoint measurements of the default bench")
     ap.add_argument("--variant", type=int, default=0, choices=list(range(12)))
     ap.add_argument("--layout", default="rows", choices=["rows", "planes"])
     args = ap.parse_args()
