@@ -120,6 +120,7 @@ void free_marker_data(btdf_batch* bt) {
 LatticeParams base_params(const btdf_batch* bt, int c) {
     const btdf_config& k = bt->cfg[c];
     LatticeParams p{};
+    p.wait_polls = -1;   // default bound of the bounded waits
     p.nx = k.nx;
     p.ny = k.ny;
     p.nxp = bt->nxp[c];

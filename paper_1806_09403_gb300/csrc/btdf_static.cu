@@ -229,6 +229,7 @@ extern "C" int btdf_ib_forces_static(const btdf_config* cfg, const void* pops, i
     const double thick = drs > 0.0 ? drs : (c.delta == 2 ? 1.4 : c.delta == 3 ? 1.9 : 2.6);
 
     LatticeParams p{};
+    p.wait_polls = -1;   // default bound of the bounded waits
     p.nx = c.nx;
     p.ny = c.ny;
     p.nxp = (int)nxp;
