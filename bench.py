@@ -72,11 +72,16 @@ def measured_peaks():
 
 
 def kernel_source_hash():
-    """First 16 hex digits of the SHA-256 of the forward kernels' sources
-    (btdf_kernels.cu followed by btdf_device.cuh)."""
+    """First 16 hex digits of the SHA-256 of the forward kernels' code
+    (btdf_kernels.cu followed by btdf_device.cuh) with comments removed and
+    whitespace collapsed, so that only a change of the code itself
+    invalidates a profile taken on it."""
     h = hashlib.sha256()
     for f in ("btdf_kernels.cu", "btdf_device.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_1806_09403_gb300", "csrc", f), "rb").read())
+        src = open(os.path.join(ROOT, "paper_1806_09403_gb300", "csrc", f)).read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

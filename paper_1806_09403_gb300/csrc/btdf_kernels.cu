@@ -776,8 +776,11 @@ collide_stream_tma_kernel(const __grid_constant__ CUtensorMap tmap, const T* __r
 // pulls the 9 populations of its node, forms rho and u* (Eqs. 9-10) and its
 // weighted share of the interpolation (Eq. 14); a segmented shuffle reduction
 // completes D_I rho and D_I u*, and the group's first lane writes
-// F_b = 2 rho_l (U_b - D_I u*) (Eq. 20).  The kernel lets the LBM kernel
-// launch at once: only band nodes there wait for these forces.
+// F_b = 2 rho_l (U_b - D_I u*) (Eq. 20).  Launched as a programmatic
+// dependent of the previous LBM kernel, it loads its marker tables while that
+// kernel drains and waits for it before the pulls; right after that wait it
+// lets its own dependent, the next LBM kernel, launch: only band nodes there
+// wait for these forces.
 
 // Body of the IB kernel for marker m of this lane's group, on the lattice
 // described by p whose populations start at g.
