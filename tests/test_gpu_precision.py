@@ -15,8 +15,10 @@
   0.144 at U = 0.05 (where it locks the shedding in and grows without bound)
   but 0.36 at U = 0.02, outside the shedding band.  The paper does not state
   its U.
-* The same FP32 run with the convective outlet the paper uses: St, Cd and
-  the lift amplitude of Table 3 within 2%.
+* The same runs with the convective outlet the paper uses: FP32 against
+  St, Cd and the lift amplitude of Table 3 within 2%; FP16 and BF16 against
+  FP32 within 1% in all three (FP16 holds it, BF16 misses the lift
+  amplitude: an expected failure).
 * The Strouhal number and mean drag of FP16 and BF16 storage against the FP32
   path on the same domain, against the 1 % bar of the mixed-precision form:
   FP16 (scaled by 2^10) holds it over the long run; BF16 (8-bit significand)
@@ -170,19 +172,29 @@ def test_long_run_mixed_against_fp32(long_runs, name):
     assert abs(cd / cd32 - 1.0) <= 1e-2
 
 
-def test_long_run_convective_outlet_against_table3():
-    """The same FP32 long run with the convective outlet Sec. 5.2 names
-    (U = u_in, implicit upwind) instead of the zero-gradient one: St, mean
-    Cd and the lift amplitude of Table 3 (BTDF, Re = 200) within 2% (the
-    table prints three significant digits; the outlet's speed and
-    discretisation are a reading)."""
+@pytest.fixture(scope="module")
+def convective_runs():
+    """The paper-domain long run with the convective outlet Sec. 5.2 names
+    (U = u_in, implicit upwind), in FP32, FP16 and BF16 storage."""
     _build.build()
     case = W.paper_domain_cylinder(re=200.0, delta=3, u=U_LONG)
     case.bc_x = W.BCX_CONVECTIVE
-    lat = B.Lattice.from_case(case, history_len=LONG)
-    lat.step(LONG)
-    cd, cl = coefficients(case, *lat.forces(0, 0, LONG))
-    lat.close()
+    out = {}
+    for storage, name in ((B.BTDF_F32, "f32"), (B.BTDF_F16DEV, "f16"), (B.BTDF_BF16DEV, "bf16")):
+        lat = B.Lattice.from_case(case, storage=storage, history_len=LONG)
+        lat.step(LONG)
+        out[name] = coefficients(case, *lat.forces(0, 0, LONG))
+        lat.close()
+    return case, out
+
+
+def test_long_run_convective_outlet_against_table3(convective_runs):
+    """The FP32 long run with the convective outlet: St, mean Cd and the lift
+    amplitude of Table 3 (BTDF, Re = 200) within 2% (the table prints three
+    significant digits; the outlet's speed and discretisation are a
+    reading)."""
+    case, out = convective_runs
+    cd, cl = out["f32"]
     skip = LONG // 2
     st, periods = strouhal(cl, case.u_in, case.D, skip)
     cd_mean = float(cd[skip:].mean())
@@ -196,3 +208,29 @@ def test_long_run_convective_outlet_against_table3():
     assert abs(cd_mean / t3["re200_cd_mean"] - 1.0) <= 0.02
     assert abs(amp / t3["re200_cl_amp"] - 1.0) <= 0.02
 
+
+@pytest.mark.parametrize("name", [
+    "f16",
+    pytest.param("bf16", marks=pytest.mark.xfail(
+        strict=False, reason="BF16 storage (8-bit significand) misses the 1% bar of the "
+                             "mixed-precision form in the lift amplitude")),
+])
+def test_long_run_convective_mixed_against_fp32(convective_runs, name):
+    """FP16 / BF16 storage against FP32 on the convective-outlet long run:
+    Strouhal number, mean drag and lift amplitude within 1% (the bar of the
+    mixed-precision form: Cd, Cl and St)."""
+    case, out = convective_runs
+    skip = LONG // 2
+    st32, _ = strouhal(out["f32"][1], case.u_in, case.D, skip)
+    st, periods = strouhal(out[name][1], case.u_in, case.D, skip)
+    cd32 = float(out["f32"][0][skip:].mean())
+    cd = float(out[name][0][skip:].mean())
+    amp32 = shedding_amplitude(out["f32"][1], case.u_in, case.D, skip)
+    amp = shedding_amplitude(out[name][1], case.u_in, case.D, skip)
+    print(f"\n[{name}, convective outlet] vs f32 over {LONG} steps: St {st:.4f} vs {st32:.4f} "
+          f"({abs(st / st32 - 1):.2e}), mean Cd {cd:.4f} vs {cd32:.4f} ({abs(cd / cd32 - 1):.2e}), "
+          f"Cl amplitude {amp:.4f} vs {amp32:.4f} ({abs(amp / amp32 - 1):.2e})")
+    assert periods >= 10
+    assert abs(st / st32 - 1.0) <= 1e-2
+    assert abs(cd / cd32 - 1.0) <= 1e-2
+    assert abs(amp / amp32 - 1.0) <= 1e-2
