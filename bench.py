@@ -469,7 +469,8 @@ def drag_error(B, case, storage, stream, sim_hist, n):
 
 
 VARIANT_NAMES = {1: "reg4", 2: "reg2", 3: "tma8x2", 4: "tma8x3", 5: "tma16x2", 6: "reg4pf",
-                 7: "reg2pf", 8: "reg1", 9: "reg2o", 10: "reg2o_l2pf", 11: "reg4_l2pf"}
+                 7: "reg2pf", 8: "reg1", 9: "reg2o", 10: "reg2o_l2pf", 11: "reg4_l2pf",
+                 12: "tma_ws8x2", 13: "tma_ws7x3"}
 
 
 def our_arm(args):
@@ -740,7 +741,7 @@ def main():
                     help="skip the FP16 / BF16 storage lines of the default bench")
     ap.add_argument("--no-extras", dest="extras", action="store_false",
                     help="skip the batched-form and adjoint measurements of the default bench")
-    ap.add_argument("--variant", type=int, default=0, choices=list(range(12)))
+    ap.add_argument("--variant", type=int, default=0, choices=list(range(14)))
     ap.add_argument("--layout", default="rows", choices=["rows", "planes"])
     args = ap.parse_args()
     if args.warmup < 3:

@@ -260,7 +260,7 @@ int btdf_profile_read(btdf_ctx *ctx, double *ms_ib, double *ms_lbm, int64_t *lau
 
 /* Number of collide-stream variants, 0 (automatic) included: the length of
  * btdf_autotune's ms output. */
-#define BTDF_VARIANT_COUNT 12
+#define BTDF_VARIANT_COUNT 14
 
 /* Variant of the fused collide-stream kernel.  Results do not depend on it.
  *   0 automatic (2 for FP32 storage, 1 for FP16 / BF16)
@@ -276,17 +276,22 @@ int btdf_profile_read(btdf_ctx *ctx, double *ms_ib, double *ms_lbm, int64_t *lau
  *  10 as 9, and each warp prefetches into L2 the row segment that a warp
  *     half a wave later will process
  *  11 as 1, with the L2 prefetch of 10
+ *  12 warp-specialized TMA CTAs: 128 x 8 node tiles handed out one at a time
+ *     from a device counter, one producer warp issuing the loads, 8 warps
+ *     computing rows, 2 pipeline stages, 3 resident blocks per SM
+ *  13 as 12 with 128 x 7 node tiles, 7 computing warps and 3 pipeline
+ *     stages, 3 resident blocks per SM
  * grid_blocks caps the grid, counted in blocks of the variant: 256 threads,
- * or 128 for variant 2 and, with FP16 / BF16 storage, variants 1 and 8-11.
- * 0 = default:
+ * or 128 for variant 2 and, with FP16 / BF16 storage, variants 1 and 8-11,
+ * or 288 for variant 12.  0 = default:
  * one 32 x NPL-node row segment per warp for variants 1, 2 and 8-11, so the
  * block scheduler balances the SMs; SM count x resident blocks per SM for
- * the persistent variants 3-7.
+ * the persistent variants 3-7, 12 and 13.
  * Synchronizes and drops cached CUDA graphs.
  * Errors: EINVAL (unknown variant, TMA variant without tensor maps). */
 int btdf_tune(btdf_ctx *ctx, int32_t variant, int32_t grid_blocks);
 
-/* Bound of the TMA-tiled variants' (3-5) per-stage waits, in polls of the
+/* Bound of the TMA-tiled variants' (3-5, 12, 13) per-stage waits, in polls of the
  * stage's mbarrier: polls < 0 restores the default (about a second of
  * polling); 0 makes every such wait give up at once.  A wait that gives up
  * records BTDF_ETIMEOUT in the status word (reported by the next btdf_sync),

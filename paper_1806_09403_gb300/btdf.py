@@ -42,7 +42,7 @@ EXPORTS = [
     "btdf_set_wait_limit",
 ]
 STATIC_MAX_MARKERS = 2048
-VARIANT_COUNT = 12          # BTDF_VARIANT_COUNT: variants 0 (automatic) .. 11, see btdf_tune
+VARIANT_COUNT = 14          # BTDF_VARIANT_COUNT: variants 0 (automatic) .. 13, see btdf_tune
 STATE_HEADER_BYTES = 48
 
 

@@ -180,6 +180,7 @@ struct btdf_ctx {
     double2* d_hist = nullptr;
     unsigned long long* d_step = nullptr;
     int* d_status = nullptr;
+    unsigned* d_sched = nullptr;         // tile tickets of the warp-specialized TMA kernel
     float* d_outlet = nullptr;         // [9][ny] previous outlet column (convective outlet)
     float2* d_box = nullptr;           // perimeter velocities of the prescribed-velocity box
     std::vector<MarkerAux> aux_host;
@@ -202,7 +203,7 @@ struct btdf_ctx {
     int variant = kVarAuto;              // LBM kernel variant (btdf_tune)
     int grid_override = 0;               // 0: SMs x resident blocks
     bool tma_ok = false;                 // tensor maps encoded
-    CUtensorMap tmap[2][2];              // [buffer][box of 10 / 18 rows]
+    CUtensorMap tmap[2][3];              // [buffer][box of 10 / 18 / 9 rows]
 
     bool prof = false;
     std::vector<cudaEvent_t> ev;         // 3 per profiled step
@@ -321,7 +322,12 @@ void free_tape(btdf_ctx* ctx) {
     T.gen = gen + 1;
 }
 
-bool is_tma(int v) { return v == kVarTma8x2 || v == kVarTma8x3 || v == kVarTma16x2; }
+bool is_tma(int v) {
+    return v == kVarTma8x2 || v == kVarTma8x3 || v == kVarTma16x2 || v == kVarTmaWs8x2 || v == kVarTmaWs7x3;
+}
+
+// Tensor map of a TMA variant: boxes of 10, 18 and 9 rows.
+int tmap_index(int v) { return v == kVarTma16x2 ? 1 : v == kVarTmaWs7x3 ? 2 : 0; }
 
 LatticeParams lattice_params(const btdf_ctx* ctx) {
     LatticeParams p{};
@@ -377,6 +383,7 @@ LatticeParams lattice_params(const btdf_ctx* ctx) {
     p.step = ctx->d_step;
     p.status = ctx->d_status;
     p.wait_polls = ctx->wait_polls;
+    p.sched = ctx->d_sched;
     p.nbody = ctx->nmark > 0 ? (int)ctx->bodies.size() : 0;
     p.hist_len = ctx->cfg.history_len;
     p.body_ptr = ctx->d_body_ptr;
@@ -438,7 +445,7 @@ int enqueue_step(btdf_ctx* ctx, cudaStream_t st, bool pull, int cur, bool prof) 
     if (ctx->d_box && (is_tma(v) || v == kVarReg4Pf || v == kVarReg2Pf)) v = kVarReg4;
     if (is_tma(v)) {
         const int grid = ctx->grid_override > 0 ? ctx->grid_override : (int)ctx->tma_grid[v];
-        CK(launch_collide_stream_tma(ctx->cfg.storage, v, &ctx->tmap[cur][v == kVarTma16x2 ? 1 : 0],
+        CK(launch_collide_stream_tma(ctx->cfg.storage, v, &ctx->tmap[cur][tmap_index(v)],
                                      ctx->g[cur], ctx->g[1 - cur], p, grid, pdl, st));
     } else {
         // Register variants.  Default grid: one row segment per warp.  SMs
@@ -502,9 +509,9 @@ bool encode_tensor_maps(btdf_ctx* ctx) {
     const cuuint64_t strides[2] = {(cuuint64_t)ctx->nxp * ctx->elem * (interleaved ? 9 : 1),
                                    (cuuint64_t)(interleaved ? ctx->nxp : ctx->plane) * ctx->elem};
     const cuuint32_t estr[3] = {1, 1, 1};
-    const int rows[2] = {tma_box_rows(kVarTma8x2), tma_box_rows(kVarTma16x2)};
+    const int rows[3] = {tma_box_rows(kVarTma8x2), tma_box_rows(kVarTma16x2), tma_box_rows(kVarTmaWs7x3)};
     for (int b = 0; b < 2; b++)
-        for (int r = 0; r < 2; r++) {
+        for (int r = 0; r < 3; r++) {
             const cuuint32_t box[3] = {(cuuint32_t)(kSeg + 2 * tma_halo(ctx->cfg.storage)),
                                        (cuuint32_t)rows[r], 9};
             if (encode(&ctx->tmap[b][r], dt, 3, ctx->g[b], dims, strides, box, estr,
@@ -975,6 +982,7 @@ int btdf_create(const btdf_config* cfg, void* stream, btdf_ctx** out) {
     *ctx->status_pin = 0;
     if (dalloc(ctx, &ctx->d_step, sizeof(unsigned long long)) != cudaSuccess ||
         dalloc(ctx, &ctx->d_status, sizeof(int)) != cudaSuccess ||
+        dalloc(ctx, &ctx->d_sched, 2 * sizeof(unsigned)) != cudaSuccess ||
         (c.bc_x == BTDF_BCX_CONVECTIVE && dalloc(ctx, &ctx->d_outlet, sizeof(float) * 9 * c.ny) != cudaSuccess) ||
         (c.bc_x == BTDF_BCX_BOX && dalloc(ctx, &ctx->d_box, sizeof(float2) * (2 * c.nx + 2 * (c.ny - 2))) != cudaSuccess))
         return bail(BTDF_ECUDA);
@@ -982,6 +990,7 @@ int btdf_create(const btdf_config* cfg, void* stream, btdf_ctx** out) {
         return bail(BTDF_ECUDA);
     if (cudaMemsetAsync(ctx->d_step, 0, sizeof(unsigned long long), ctx->stream) != cudaSuccess ||
         cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream) != cudaSuccess ||
+        cudaMemsetAsync(ctx->d_sched, 0, 2 * sizeof(unsigned), ctx->stream) != cudaSuccess ||
         cudaStreamSynchronize(ctx->stream) != cudaSuccess)
         return bail(BTDF_ECUDA);
     *out = ctx;
@@ -998,6 +1007,7 @@ int btdf_destroy(btdf_ctx* ctx) {
     dfree(ctx, ctx->g[1]);
     dfree(ctx, ctx->d_step);
     dfree(ctx, ctx->d_status);
+    dfree(ctx, ctx->d_sched);
     dfree(ctx, ctx->d_outlet);
     dfree(ctx, ctx->d_box);
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
@@ -1032,6 +1042,7 @@ int btdf_init_fields(btdf_ctx* ctx, const double* rho, const double* ux, const d
         CK(launch_init_equilibrium(ctx->cfg.storage, ctx->g[0], p, d, d + nn, d + 2 * nn, st));
         CK(cudaMemsetAsync(ctx->d_step, 0, sizeof(unsigned long long), st));
         CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
+        CK(cudaMemsetAsync(ctx->d_sched, 0, 2 * sizeof(unsigned), st));
         CK(cudaStreamSynchronize(st));
         return BTDF_OK;
     };

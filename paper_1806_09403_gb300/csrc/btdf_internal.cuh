@@ -151,6 +151,9 @@ struct LatticeParams {
     // Polls before a TMA stage wait gives up (< 0: the default bound of about
     // a second); set by btdf_set_wait_limit to exercise the timeout path.
     int wait_polls;
+    // Tile tickets of the warp-specialized TMA kernel: [0] next tile, [1]
+    // CTAs finished; both zero between launches (null: kernel unavailable).
+    unsigned* sched;
     // Force on each body (Eq. 27), reduced in FP64 by block 0 of the LBM kernel.
     int nbody;
     int hist_len;
@@ -215,7 +218,9 @@ enum : int {
     kVarReg2Occ = 9,   // 2 nodes per lane, 5 blocks per SM (<= 48 registers)
     kVarReg2OccPf = 10, // as 9, each warp also prefetches a later row segment into L2
     kVarReg4L2Pf = 11, // as 1, with the L2 prefetch of 10
-    kVarCount = 12
+    kVarTmaWs8x2 = 12, // TMA tiles of 8 rows, a producer warp, 2 stages, <= 72 registers
+    kVarTmaWs7x3 = 13, // TMA tiles of 7 rows, a producer warp, 3 stages, <= 80 registers
+    kVarCount = 14
 };
 // map: 3-D tensor map (x, y, population) of the input buffer with box
 // (128 + 2 * tma_halo(storage), tma_box_rows(variant), 9).

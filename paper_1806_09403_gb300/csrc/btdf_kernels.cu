@@ -35,8 +35,11 @@ namespace {
 // ---- the fused LBM kernel ----------------------------------------------------
 
 // Force on every body (Eq. 27) from the Lagrangian forces of this step, in
-// FP64, and the step counter.  Run by block 0 of the LBM kernel after its
-// lattice work, once the IB kernel has finished.
+// FP64, and the step counter.  Run by block 0 of the LBM kernel (after its
+// lattice work; first, in the persistent warp-specialized kernel) once the IB
+// kernel has finished.  A warp takes four bodies per pass so that their loads
+// overlap; each body's sum keeps one order (lane-strided partial sums, then a
+// butterfly), whichever kernel runs it.
 __device__ void body_forces_and_step(const LatticeParams& p) {
     __shared__ unsigned long long s_step;
     if (p.nbody > 0) cudaGridDependencySynchronize();
@@ -45,21 +48,41 @@ __device__ void body_forces_and_step(const LatticeParams& p) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const long long slot = (long long)(s_step % (unsigned long long)(p.hist_len > 0 ? p.hist_len : 1)) *
                            p.nbody;
-    for (int b = warp; b < p.nbody; b += nwarps) {
-        double sx = 0.0, sy = 0.0;
-        for (int k = p.body_ptr[b] + lane; k < p.body_ptr[b + 1]; k += 32) {
-            const float2 F = p.F[k];
-            sx += (double)F.x;
-            sy += (double)F.y;
+    constexpr int U = 4;
+    for (int b0 = warp; b0 < p.nbody; b0 += U * nwarps) {
+        int lo[U], hi[U];
+        double sx[U], sy[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int b = b0 + u * nwarps;
+            lo[u] = b < p.nbody ? p.body_ptr[b] + lane : 0;
+            hi[u] = b < p.nbody ? p.body_ptr[b + 1] : 0;
+            sx[u] = sy[u] = 0.0;
+        }
+        for (int j = 0;; j += 32) {
+            bool any = false;
+#pragma unroll
+            for (int u = 0; u < U; u++)
+                if (lo[u] + j < hi[u]) {
+                    const float2 F = p.F[lo[u] + j];
+                    sx[u] += (double)F.x;
+                    sy[u] += (double)F.y;
+                    any = true;
+                }
+            if (!__any_sync(kFull, any)) break;
         }
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            sx += __shfl_xor_sync(kFull, sx, off);
-            sy += __shfl_xor_sync(kFull, sy, off);
-        }
-        if (lane == 0) {
-            const double sc = p.body_scale[b];
-            p.hist[slot + b] = make_double2(-sx * sc, -sy * sc);
+        for (int u = 0; u < U; u++) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                sx[u] += __shfl_xor_sync(kFull, sx[u], off);
+                sy[u] += __shfl_xor_sync(kFull, sy[u], off);
+            }
+            const int b = b0 + u * nwarps;
+            if (lane == 0 && b < p.nbody) {
+                const double sc = p.body_scale[b];
+                p.hist[slot + b] = make_double2(-sx[u] * sc, -sy[u] * sc);
+            }
         }
     }
     if (threadIdx.x == 0 && p.step != nullptr) *p.step = s_step + 1ull;
@@ -620,6 +643,105 @@ __device__ __forceinline__ void tma_issue(const CUtensorMap* map, unsigned char*
     tma_load_3d(stages + stage * C::STAGE_STRIDE, map, &bars[stage], tx * C::TW - C::H, ty * TH - 1, 0);
 }
 
+// One row of a TMA tile (warp `warp` of the tile's TH rows): the nine
+// pulled planes from the shared-memory stage (x and y neighbours included;
+// wrap rows of a periodic lattice and the two row ends from global memory),
+// then collide_store.  C is the tile configuration (TmaCfg); seg is the row's
+// band segment (band_segment()).
+template <typename T, typename C>
+__device__ __forceinline__ void tma_tile_row(const T* __restrict__ tile, const T* __restrict__ gin,
+                                             T* __restrict__ gout, const LatticeParams& p, int x0t,
+                                             int y0, int warp, int lane, int seg) {
+    const int y = y0 + warp;
+    if (y < p.ny) {
+        const int x0 = x0t + 4 * lane;
+        const bool live = x0 < p.nxp;
+        float f[9][4];
+        if (y > 0 && y < p.ny - 1) {
+            // Interior row: all nine sources in the tile, shifts known at
+            // compile time.
+#pragma unroll
+            for (int a = 0; a < 9; a++) {
+                const int dx = -ex(a);
+                const T* srow = tile + (a * C::BY + warp + 1 - ey(a)) * C::BX + C::H;
+                Raw<T>::template ldv<4>(srow + 4 * lane, f[a]);
+                if (dx < 0) {
+                    float prev = __shfl_up_sync(kFull, f[a][3], 1);
+                    if (lane == 0) prev = Raw<T>::ld1s(srow - 1);
+                    f[a][3] = f[a][2]; f[a][2] = f[a][1]; f[a][1] = f[a][0]; f[a][0] = prev;
+                } else if (dx > 0) {
+                    float next = __shfl_down_sync(kFull, f[a][0], 1);
+                    if (lane == 31) next = Raw<T>::ld1s(srow + C::TW);
+                    f[a][0] = f[a][1]; f[a][1] = f[a][2]; f[a][2] = f[a][3]; f[a][3] = next;
+                }
+            }
+        } else {
+#pragma unroll
+        for (int a = 0; a < 9; a++) {
+            int pa = a, sy = y - ey(a), dx = -ex(a);
+            if (sy < 0 || sy >= p.ny) {
+                float unused;
+                y_source(a, y, p, pa, sy, dx, unused);
+            }
+            const int r = sy - y0 + 1;                  // row inside the tile
+            float v[4];
+            if (r >= 0 && r < C::BY) {                  // from shared memory
+                const T* srow = tile + (pa * C::BY + r) * C::BX + C::H;
+                Raw<T>::template ldv<4>(srow + 4 * lane, v);   // same bank group per lane
+                if (dx < 0) {
+                    float prev = __shfl_up_sync(kFull, v[3], 1);
+                    if (lane == 0) prev = Raw<T>::ld1s(srow - 1);
+                    v[3] = v[2]; v[2] = v[1]; v[1] = v[0]; v[0] = prev;
+                } else if (dx > 0) {
+                    float next = __shfl_down_sync(kFull, v[0], 1);
+                    if (lane == 31) next = Raw<T>::ld1s(srow + C::TW);
+                    v[0] = v[1]; v[1] = v[2]; v[2] = v[3]; v[3] = next;
+                }
+            } else {                                    // periodic wrap row: global
+                const T* grow = gin + p.poff[pa] + (unsigned)sy * p.rs;
+                if (live) Raw<T>::template ldv<4>(grow + x0, v);
+                else v[0] = v[1] = v[2] = v[3] = 0.0f;
+                if (dx < 0) {
+                    float prev = __shfl_up_sync(kFull, v[3], 1);
+                    if (lane == 0) prev = (live && x0 > 0) ? Raw<T>::ld1(grow + x0 - 1) : 0.0f;
+                    v[3] = v[2]; v[2] = v[1]; v[1] = v[0]; v[0] = prev;
+                } else if (dx > 0) {
+                    float next = __shfl_down_sync(kFull, v[0], 1);
+                    if (lane == 31) next = (live && x0 + 4 < p.nxp) ? Raw<T>::ld1(grow + x0 + 4) : 0.0f;
+                    v[0] = v[1]; v[1] = v[2]; v[2] = v[3]; v[3] = next;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 4; i++) f[a][i] = v[i];
+        }
+        }
+        if (p.bcy == kBcyNoslip && (y == 0 || y == p.ny - 1)) {
+#pragma unroll
+            for (int a = 0; a < 9; a++) {
+                const int sy = y - ey(a);
+                if (sy < 0 || sy >= p.ny) {
+                    const float add = -6.0f * wt(a) * p.eur[a] * Raw<T>::kScale;
+#pragma unroll
+                    for (int i = 0; i < 4; i++) f[a][i] += add;
+                }
+            }
+        }
+        if (live && x0 < p.nx && (x0 == 0 || x0 + 3 >= p.nx - 1)) {
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                const int x = x0 + i;
+                if (x == 0 || x == p.nx - 1) {
+                    float fe[9];
+                    pull_node<T>(gin, p, x, y, fe);
+#pragma unroll
+                    for (int a = 0; a < 9; a++) f[a][i] = fe[a] * Raw<T>::kScale;
+                }
+            }
+        }
+        collide_store<T, 4>(f, gout, p, y, x0t, x0, live, seg);
+    }
+}
+
 template <typename T, int TH, int S>
 __global__ void __launch_bounds__(32 * TH, TH == 8 ? 2 : 1)
 collide_stream_tma_kernel(const __grid_constant__ CUtensorMap tmap, const T* __restrict__ gin,
@@ -666,96 +788,9 @@ collide_stream_tma_kernel(const __grid_constant__ CUtensorMap tmap, const T* __r
             return;
         }
         const T* tile = (const T*)(stages + st * C::STAGE_STRIDE);
-        const int x0t = (t % ntx) * C::TW, y0 = (t / ntx) * TH;
-        const int y = y0 + warp;
-        if (y < p.ny) {
-            const int x0 = x0t + 4 * lane;
-            const bool live = x0 < p.nxp;
-            const int seg = band_segment(p, y, x0t);
-            float f[9][4];
-            if (y > 0 && y < p.ny - 1) {
-                // Interior row: all nine sources in the tile, shifts known at
-                // compile time.
-#pragma unroll
-                for (int a = 0; a < 9; a++) {
-                    const int dx = -ex(a);
-                    const T* srow = tile + (a * C::BY + warp + 1 - ey(a)) * C::BX + C::H;
-                    Raw<T>::template ldv<4>(srow + 4 * lane, f[a]);
-                    if (dx < 0) {
-                        float prev = __shfl_up_sync(kFull, f[a][3], 1);
-                        if (lane == 0) prev = Raw<T>::ld1s(srow - 1);
-                        f[a][3] = f[a][2]; f[a][2] = f[a][1]; f[a][1] = f[a][0]; f[a][0] = prev;
-                    } else if (dx > 0) {
-                        float next = __shfl_down_sync(kFull, f[a][0], 1);
-                        if (lane == 31) next = Raw<T>::ld1s(srow + C::TW);
-                        f[a][0] = f[a][1]; f[a][1] = f[a][2]; f[a][2] = f[a][3]; f[a][3] = next;
-                    }
-                }
-            } else {
-#pragma unroll
-            for (int a = 0; a < 9; a++) {
-                int pa = a, sy = y - ey(a), dx = -ex(a);
-                if (sy < 0 || sy >= p.ny) {
-                    float unused;
-                    y_source(a, y, p, pa, sy, dx, unused);
-                }
-                const int r = sy - y0 + 1;                  // row inside the tile
-                float v[4];
-                if (r >= 0 && r < C::BY) {                  // from shared memory
-                    const T* srow = tile + (pa * C::BY + r) * C::BX + C::H;
-                    Raw<T>::template ldv<4>(srow + 4 * lane, v);   // same bank group per lane
-                    if (dx < 0) {
-                        float prev = __shfl_up_sync(kFull, v[3], 1);
-                        if (lane == 0) prev = Raw<T>::ld1s(srow - 1);
-                        v[3] = v[2]; v[2] = v[1]; v[1] = v[0]; v[0] = prev;
-                    } else if (dx > 0) {
-                        float next = __shfl_down_sync(kFull, v[0], 1);
-                        if (lane == 31) next = Raw<T>::ld1s(srow + C::TW);
-                        v[0] = v[1]; v[1] = v[2]; v[2] = v[3]; v[3] = next;
-                    }
-                } else {                                    // periodic wrap row: global
-                    const T* grow = gin + p.poff[pa] + (unsigned)sy * p.rs;
-                    if (live) Raw<T>::template ldv<4>(grow + x0, v);
-                    else v[0] = v[1] = v[2] = v[3] = 0.0f;
-                    if (dx < 0) {
-                        float prev = __shfl_up_sync(kFull, v[3], 1);
-                        if (lane == 0) prev = (live && x0 > 0) ? Raw<T>::ld1(grow + x0 - 1) : 0.0f;
-                        v[3] = v[2]; v[2] = v[1]; v[1] = v[0]; v[0] = prev;
-                    } else if (dx > 0) {
-                        float next = __shfl_down_sync(kFull, v[0], 1);
-                        if (lane == 31) next = (live && x0 + 4 < p.nxp) ? Raw<T>::ld1(grow + x0 + 4) : 0.0f;
-                        v[0] = v[1]; v[1] = v[2]; v[2] = v[3]; v[3] = next;
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < 4; i++) f[a][i] = v[i];
-            }
-            }
-            if (p.bcy == kBcyNoslip && (y == 0 || y == p.ny - 1)) {
-#pragma unroll
-                for (int a = 0; a < 9; a++) {
-                    const int sy = y - ey(a);
-                    if (sy < 0 || sy >= p.ny) {
-                        const float add = -6.0f * wt(a) * p.eur[a] * Raw<T>::kScale;
-#pragma unroll
-                        for (int i = 0; i < 4; i++) f[a][i] += add;
-                    }
-                }
-            }
-            if (live && x0 < p.nx && (x0 == 0 || x0 + 3 >= p.nx - 1)) {
-#pragma unroll
-                for (int i = 0; i < 4; i++) {
-                    const int x = x0 + i;
-                    if (x == 0 || x == p.nx - 1) {
-                        float fe[9];
-                        pull_node<T>(gin, p, x, y, fe);
-#pragma unroll
-                        for (int a = 0; a < 9; a++) f[a][i] = fe[a] * Raw<T>::kScale;
-                    }
-                }
-            }
-            collide_store<T, 4>(f, gout, p, y, x0t, x0, live, seg);
-        }
+        const int y0 = (t / ntx) * TH, x0t = (t % ntx) * C::TW;
+        const int seg = y0 + warp < p.ny ? band_segment(p, y0 + warp, x0t) : -1;
+        tma_tile_row<T, C>(tile, gin, gout, p, x0t, y0, warp, lane, seg);
         // Every thread is done with this stage: refill it with tile k + S.
         __syncthreads();
         if (tid == 0) {
@@ -768,6 +803,158 @@ collide_stream_tma_kernel(const __grid_constant__ CUtensorMap tmap, const T* __r
         }
     }
     if (blockIdx.x == 0) body_forces_and_step(p);
+}
+
+// ---- the warp-specialized TMA LBM kernel ----------------------------------------
+
+// The tiles of collide_stream_tma_kernel, handed out dynamically: warp TH of
+// the CTA is the producer, warps 0..TH-1 compute rows.  The producer takes
+// tile indices from a global ticket counter (p.sched[0], one stage use
+// ahead), waits until the consumers have released the stage it refills (one
+// "empty" mbarrier per stage, TH arrivals), writes the tile index beside the
+// stage, issues the tile's 3-D load on the stage's "full" mbarrier, looks up
+// the band segment of each of the tile's rows into shared memory and adds the
+// stage's second arrival.  Consumer warps walk the stages in order: wait for
+// "full", compute their row, arrive on "empty".  No CTA-wide barrier sits
+// between tiles, so a warp can run up to S tiles ahead of the slowest, and
+// tiles go to CTAs as they free up (the block scheduler's balancing, in a
+// persistent grid).  A ticket past the last tile makes the producer post
+// index -1, which ends the consumers.  The last CTA to finish resets both
+// counters (p.sched[1] counts finished CTAs) for the next launch.
+//
+// Every wait is bounded.  A consumer that gives up records BTDF_ETIMEOUT and
+// raises a shared halt flag that ends every other wait of the CTA; the
+// producer then waits (with the full bound) for each of its copies still in
+// flight before the CTA exits.
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait on phase `parity` of `bar` that also ends when *halt is set.
+__device__ __forceinline__ bool mbar_wait_haltable(unsigned long long* bar, unsigned parity,
+                                                    unsigned limit, const volatile int* halt) {
+    for (unsigned i = 0; i < limit; i++) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*halt) return false;
+    }
+    return false;
+}
+
+template <typename T, int TH, int S, int MINB>
+__global__ void __launch_bounds__(32 * (TH + 1), MINB)
+collide_stream_tma_ws_kernel(const __grid_constant__ CUtensorMap tmap, const T* __restrict__ gin,
+                             T* __restrict__ gout, LatticeParams p) {
+    cudaTriggerProgrammaticLaunchCompletion();   // as in collide_stream_kernel
+    using C = TmaCfg<T, TH, S>;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* stages =
+        (unsigned char*)(((unsigned long long)smem_raw + 1023ull) & ~1023ull);
+    unsigned long long* full = (unsigned long long*)(stages + S * C::STAGE_STRIDE);
+    unsigned long long* empty = full + S;
+    volatile int* tile_of = (volatile int*)(empty + S);   // [S] tile index per stage
+    volatile int* halt = tile_of + S;
+    volatile int* seg_of = halt + 1;                       // [S][TH] band segment per row
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    const int ntx = (p.nxp + C::TW - 1) / C::TW;
+    const int ntiles = ntx * ((p.ny + TH - 1) / TH);
+    if (tid == 0) {
+        for (int st = 0; st < S; st++) {
+            mbar_init(&full[st], 2);   // the copy's arrival and the band segments'
+            mbar_init(&empty[st], TH);
+        }
+        *halt = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // Block 0 reduces the body forces first: the other CTAs take the tiles
+    // meanwhile, whereas after its last tile the reduction (a dependent chain
+    // of loads per body) would be the launch's tail.
+    if (blockIdx.x == 0) body_forces_and_step(p);
+    // p.wait_polls >= 0 shortens the consumers' waits (a test of the timeout
+    // path); the producer's drain always keeps the full bound
+    const unsigned limit = p.wait_polls < 0 ? kWaitLimit : (unsigned)p.wait_polls;
+
+    if (warp == TH) {
+        // Producer warp.  Lane 0 holds the ticket of the next stage use
+        // (taken one use ahead, so the atomic's latency overlaps the wait for
+        // a free stage) and issues the copy; then lanes 0..TH-1 look up the
+        // band segment of each row of the tile, so that the consumers find it
+        // in shared memory beside the tile, and lane 0 adds the stage's
+        // second arrival.
+        int k = 0;   // stage uses so far
+        int t_next = lane == 0 ? (int)atomicAdd(&p.sched[0], 1u) : 0;
+        for (;; k++) {
+            const int st = k % S;
+            if (k >= S) {
+                bool ok = mbar_wait_haltable(&empty[st], (unsigned)((k / S - 1) & 1), kWaitLimit, halt);
+                ok = __all_sync(kFull, ok);
+                if (!ok) {
+                    if (lane == 0 && !*halt) {
+                        atomicOr(p.status, kStatusTimeout);
+                        *halt = 1;
+                    }
+                    break;
+                }
+                if (lane == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            }
+            if (__any_sync(kFull, *halt != 0)) break;
+            int t = __shfl_sync(kFull, t_next, 0);
+            if (t >= ntiles) t = -1;
+            if (lane == 0) {
+                tile_of[st] = t;
+                if (t < 0) {
+                    mbar_arrive(&full[st]);
+                } else {
+                    tma_issue<T, TH, S>(&tmap, stages, full, st, t, ntx);
+                    t_next = (int)atomicAdd(&p.sched[0], 1u);
+                }
+            }
+            if (t >= 0 && lane < TH) {
+                const int y = (t / ntx) * TH + lane;
+                seg_of[st * TH + lane] = y < p.ny ? band_segment(p, y, (t % ntx) * C::TW) : -1;
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&full[st]);
+            if (t < 0) {
+                k++;
+                break;
+            }
+        }
+        // After a halt, wait for the copies that may still be landing: the
+        // last use of each stage.
+        if (lane == 0 && *halt)
+            for (int j = k - S < 0 ? 0 : k - S; j < k; j++)
+                mbar_wait_bounded(&full[j % S], (unsigned)((j / S) & 1));
+    } else {
+        for (int k = 0;; k++) {
+            const int st = k % S;
+            bool ok = mbar_wait_haltable(&full[st], (unsigned)((k / S) & 1), limit, halt);
+            ok = __all_sync(kFull, ok);
+            if (!ok) {
+                if (lane == 0 && !*halt) {
+                    atomicOr(p.status, kStatusTimeout);
+                    *halt = 1;
+                }
+                break;
+            }
+            const int t = tile_of[st];
+            if (t < 0) break;
+            const int seg = seg_of[st * TH + warp];
+            const T* tile = (const T*)(stages + st * C::STAGE_STRIDE);
+            tma_tile_row<T, C>(tile, gin, gout, p, (t % ntx) * C::TW, (t / ntx) * TH, warp, lane, seg);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[st]);
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(&p.sched[1], 1u) == gridDim.x - 1) {
+            p.sched[0] = 0u;
+            p.sched[1] = 0u;
+        }
+    }
 }
 
 // ---- the IB stage -------------------------------------------------------------
@@ -1148,6 +1335,47 @@ int tma_blocks_tn() {
     return n;
 }
 
+// Shared memory of the warp-specialized kernel: the stages, alignment slack
+// and the full / empty barriers, tile indices, halt flag and band segments.
+template <typename T, int TH, int S>
+constexpr int ws_smem() {
+    return S * TmaCfg<T, TH, S>::STAGE_STRIDE + 1024 + S * (20 + 4 * TH) + 16;
+}
+
+template <typename T, int TH, int S, int MINB>
+cudaError_t tma_ws_tn(const CUtensorMap* map, const void* gin, void* gout, const LatticeParams& p,
+                      int grid, bool pdl, cudaStream_t st) {
+    using C = TmaCfg<T, TH, S>;
+    if (p.sched == nullptr) return cudaErrorInvalidValue;
+    auto kern = collide_stream_tma_ws_kernel<T, TH, S, MINB>;
+    constexpr int smem = ws_smem<T, TH, S>();
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const long long ntiles = (long long)((p.nxp + C::TW - 1) / C::TW) * ((p.ny + TH - 1) / TH);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)std::min<long long>(ntiles, (long long)grid));
+    cfg.blockDim = dim3(32 * (TH + 1));
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, *map, (const T*)gin, (T*)gout, p);
+}
+
+template <typename T, int TH, int S, int MINB>
+int tma_ws_blocks_tn() {
+    auto kern = collide_stream_tma_ws_kernel<T, TH, S, MINB>;
+    constexpr int smem = ws_smem<T, TH, S>();
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+        return 0;
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, 32 * (TH + 1), smem);
+    return n;
+}
+
 template <typename T>
 cudaError_t tma_t(int variant, const CUtensorMap* map, const void* gin, void* gout,
                   const LatticeParams& p, int grid, bool pdl, cudaStream_t st) {
@@ -1155,6 +1383,8 @@ cudaError_t tma_t(int variant, const CUtensorMap* map, const void* gin, void* go
     case kVarTma8x2: return tma_tn<T, 8, 2>(map, gin, gout, p, grid, pdl, st);
     case kVarTma8x3: return tma_tn<T, 8, 3>(map, gin, gout, p, grid, pdl, st);
     case kVarTma16x2: return tma_tn<T, 16, 2>(map, gin, gout, p, grid, pdl, st);
+    case kVarTmaWs8x2: return tma_ws_tn<T, 8, 2, 3>(map, gin, gout, p, grid, pdl, st);
+    case kVarTmaWs7x3: return tma_ws_tn<T, 7, 3, 3>(map, gin, gout, p, grid, pdl, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -1165,6 +1395,8 @@ int tma_blocks_t(int variant) {
     case kVarTma8x2: return tma_blocks_tn<T, 8, 2>();
     case kVarTma8x3: return tma_blocks_tn<T, 8, 3>();
     case kVarTma16x2: return tma_blocks_tn<T, 16, 2>();
+    case kVarTmaWs8x2: return tma_ws_blocks_tn<T, 8, 2, 3>();
+    case kVarTmaWs7x3: return tma_ws_blocks_tn<T, 7, 3, 3>();
     default: return 0;
     }
 }
@@ -1319,11 +1551,14 @@ int collide_stream_tma_blocks_per_sm(int storage, int variant) {
     }
 }
 
-int tma_box_rows(int variant) { return variant == kVarTma16x2 ? 18 : 10; }
+int tma_box_rows(int variant) {
+    return variant == kVarTma16x2 ? 18 : variant == kVarTmaWs7x3 ? 9 : 10;
+}
 int tma_halo(int storage) { return storage == kStoreF32 ? 4 : 8; }
 
 int collide_stream_block_threads(int storage, int variant) {
-    if (variant == kVarTma8x2 || variant == kVarTma8x3 || variant == kVarTma16x2)
+    if (variant == kVarTma8x2 || variant == kVarTma8x3 || variant == kVarTma16x2 ||
+        variant == kVarTmaWs8x2 || variant == kVarTmaWs7x3)
         return -1;   // the TMA kernels size their own blocks
     if (variant == kVarReg4Pf || variant == kVarReg2Pf) return kThreads;
     const int eb = storage == kStoreF32 ? 4 : 2;

@@ -283,7 +283,8 @@ def test_graph_replay_matches_direct_launches():
 
 
 VARIANTS = [(1, 0), (2, 0), (3, 0), (4, 0), (5, 0), (6, 0), (7, 0), (8, 0), (9, 0), (10, 0), (11, 0),
-            (1, 7), (2, 1), (3, 5), (5, 1), (6, 3), (7, 1), (8, 5), (9, 2), (10, 3), (11, 4)]
+            (12, 0), (13, 0), (1, 7), (2, 1), (3, 5), (5, 1), (6, 3), (7, 1), (8, 5), (9, 2), (10, 3),
+            (11, 4), (12, 1), (13, 3)]
 
 
 @pytest.mark.parametrize("storage", [B.BTDF_F32, B.BTDF_F16DEV, B.BTDF_BF16DEV])
@@ -308,7 +309,7 @@ def test_kernel_variants_agree_bitwise(storage):
         lat.tune(B.VARIANT_COUNT, 0)
 
 
-@pytest.mark.parametrize("variant", [1, 3, 5, 6, 7])
+@pytest.mark.parametrize("variant", [1, 3, 5, 6, 7, 12])
 def test_kernel_variants_periodic_and_walls(variant):
     """Wrap rows (periodic y) and wall rows in every kernel variant."""
     for bcy in (0, 1, 2):
@@ -368,13 +369,17 @@ def test_instability_is_reported():
     assert ei.value.status == B.BTDF_EUNSTABLE
 
 
-@pytest.mark.parametrize("variant", [3, 5])
+@pytest.mark.parametrize("variant", [3, 5, 12, 13])
 def test_timeout_is_reported(variant):
     """Failure detection, timeout path: with the TMA kernel's per-stage wait
     cut to zero polls every stage wait gives up, the kernel records the
     timeout, each CTA drains its own copies (full bound) and leaves, and the
-    next btdf_sync reports BTDF_ETIMEOUT (sticky).  A fresh context on the
-    same device then steps exactly like a context that never timed out."""
+    next btdf_sync reports BTDF_ETIMEOUT (sticky).  The same context, with
+    the default bound restored and its fields initialised again (which
+    clears the status), and a fresh context on the same device then step
+    exactly like a context that never timed out (for the warp-specialized
+    variants this also shows the tile counters were reset by the aborted
+    launch)."""
     case = W.small_cylinder(delta=3, seed=14)
     lat = B.Lattice.from_case(case)
     lat.step(1)                     # the first step reads in place (register kernel)
@@ -388,7 +393,10 @@ def test_timeout_is_reported(variant):
     with pytest.raises(B.BtdfError) as ei:
         lat.sync()
     assert ei.value.status == B.BTDF_ETIMEOUT
-    lat.close()
+    lat.set_wait_limit(-1)
+    lat.init_fields(*case.initial_fields())
+    lat.step(200)
+    lat.sync()
     a = B.Lattice.from_case(case)
     a.tune(variant, 0)
     a.step(200)
@@ -396,6 +404,8 @@ def test_timeout_is_reported(variant):
     b = B.Lattice.from_case(case)
     b.step(200)
     assert np.array_equal(a.field(B.FIELD_UX), b.field(B.FIELD_UX))
+    assert np.array_equal(lat.field(B.FIELD_UX), b.field(B.FIELD_UX))
+    lat.close()
     sim = O.Sim.from_case(case)
     sim.step(200)
     check_fields(a, sim)
