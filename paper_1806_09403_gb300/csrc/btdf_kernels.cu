@@ -37,9 +37,9 @@ namespace {
 // Force on every body (Eq. 27) from the Lagrangian forces of this step, in
 // FP64, and the step counter.  Run by block 0 of the LBM kernel (after its
 // lattice work; first, in the persistent warp-specialized kernel) once the IB
-// kernel has finished.  A warp takes four bodies per pass so that their loads
-// overlap; each body's sum keeps one order (lane-strided partial sums, then a
-// butterfly), whichever kernel runs it.
+// kernel has finished.  FP64 arithmetic is slow on this part and, on small
+// lattices, this reduction is on the step's critical path: one warp per body
+// and no work for absent bodies.
 __device__ void body_forces_and_step(const LatticeParams& p) {
     __shared__ unsigned long long s_step;
     if (p.nbody > 0) cudaGridDependencySynchronize();
@@ -48,41 +48,21 @@ __device__ void body_forces_and_step(const LatticeParams& p) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const long long slot = (long long)(s_step % (unsigned long long)(p.hist_len > 0 ? p.hist_len : 1)) *
                            p.nbody;
-    constexpr int U = 4;
-    for (int b0 = warp; b0 < p.nbody; b0 += U * nwarps) {
-        int lo[U], hi[U];
-        double sx[U], sy[U];
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-            const int b = b0 + u * nwarps;
-            lo[u] = b < p.nbody ? p.body_ptr[b] + lane : 0;
-            hi[u] = b < p.nbody ? p.body_ptr[b + 1] : 0;
-            sx[u] = sy[u] = 0.0;
-        }
-        for (int j = 0;; j += 32) {
-            bool any = false;
-#pragma unroll
-            for (int u = 0; u < U; u++)
-                if (lo[u] + j < hi[u]) {
-                    const float2 F = p.F[lo[u] + j];
-                    sx[u] += (double)F.x;
-                    sy[u] += (double)F.y;
-                    any = true;
-                }
-            if (!__any_sync(kFull, any)) break;
+    for (int b = warp; b < p.nbody; b += nwarps) {
+        double sx = 0.0, sy = 0.0;
+        for (int k = p.body_ptr[b] + lane; k < p.body_ptr[b + 1]; k += 32) {
+            const float2 F = p.F[k];
+            sx += (double)F.x;
+            sy += (double)F.y;
         }
 #pragma unroll
-        for (int u = 0; u < U; u++) {
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                sx[u] += __shfl_xor_sync(kFull, sx[u], off);
-                sy[u] += __shfl_xor_sync(kFull, sy[u], off);
-            }
-            const int b = b0 + u * nwarps;
-            if (lane == 0 && b < p.nbody) {
-                const double sc = p.body_scale[b];
-                p.hist[slot + b] = make_double2(-sx[u] * sc, -sy[u] * sc);
-            }
+        for (int off = 16; off > 0; off >>= 1) {
+            sx += __shfl_xor_sync(kFull, sx, off);
+            sy += __shfl_xor_sync(kFull, sy, off);
+        }
+        if (lane == 0) {
+            const double sc = p.body_scale[b];
+            p.hist[slot + b] = make_double2(-sx * sc, -sy * sc);
         }
     }
     if (threadIdx.x == 0 && p.step != nullptr) *p.step = s_step + 1ull;
