@@ -85,10 +85,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(workload, storage):
+def ncu_traffic(workload, storage, variant):
     """DRAM bytes per launch of the collide-stream kernel from the committed
-    ncu summary, or None when the summary is missing or was taken on another
-    version of the kernel source."""
+    ncu summary, or None when the summary is missing, was taken on another
+    version of the kernel source or on another kernel variant."""
     tag = {0: "f32", 1: "f16", 2: "bf16"}[storage]
     path = os.path.join(ROOT, "profiles", f"ncu_collide_stream_{workload}_{tag}.txt")
     if not os.path.exists(path):
@@ -96,7 +96,8 @@ def ncu_traffic(workload, storage):
     txt = open(path).read()
     h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
     t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
-    if not h or not t or h.group(1) != kernel_source_hash():
+    v = re.search(r"^variant:\s*(\S+)", txt, re.M)
+    if not h or not t or not v or h.group(1) != kernel_source_hash() or v.group(1) != variant:
         return None
     return float(t.group(1))
 
@@ -518,7 +519,7 @@ def our_arm(args):
         peak, peak_src = float(peaks["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
     else:
         peak, peak_src = 6800.0, "fallback 6.8 TB/s"
-    traffic = ncu_traffic(args.workload, storage)
+    traffic = ncu_traffic(args.workload, storage, m["variant"])
 
     # ---- warm sustained rate through CUDA graphs (no flush) ----
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -586,7 +587,7 @@ def our_arm(args):
                                      hist)
             l2.close()
             mm["frac"] = mm["achieved_gbs"] / peak
-            mm["traffic"] = ncu_traffic(args.workload, st)
+            mm["traffic"] = ncu_traffic(args.workload, st, mm["variant"])
             mixed[name] = mm
 
     # ---- the batched and the differentiated forms (one GPU, rank 0) ----
