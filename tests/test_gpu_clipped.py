@@ -34,10 +34,11 @@ from paper_1806_09403_gb300 import btdf as B  # noqa: E402
 STEPS = 1000
 VEL_TOL = 1e-5
 CD_TOL = 1e-4
-# (variant, layout): 4 and 2 nodes per lane, the TMA-tiled kernel and the
-# prefetching 4-node kernel, across both layouts
+# (variant, layout): 4 and 2 nodes per lane, the TMA-tiled kernel, the
+# prefetching 4-node kernel and the two warp-specialized TMA kernels, across
+# both layouts
 RUNS = [(1, B.LAYOUT_ROWS), (2, B.LAYOUT_PLANES), (3, B.LAYOUT_ROWS), (11, B.LAYOUT_PLANES),
-        (9, B.LAYOUT_ROWS)]
+        (9, B.LAYOUT_ROWS), (12, B.LAYOUT_PLANES), (13, B.LAYOUT_ROWS)]
 
 
 @pytest.fixture(scope="module", autouse=True)

@@ -1,6 +1,8 @@
 """Parity at the full sizes of the benchmarked configurations, in the launch
-configuration bench.py times (default variant, one row segment per warp,
-CUDA-graph replay):
+configurations bench.py times (CUDA-graph replay; on the 8192 x 4096 lattice
+the collide-stream variant its autotuner keeps, 11 for FP32 and the
+warp-specialized TMA kernel 12 for FP16 / BF16, each also checked bitwise
+against the default variant):
 
 * the 8192 x 4096 lattice with 400 cylinders (D = 20, 63 markers each),
   FP32, against the FP64 oracle over 100 steps: velocity field and the drag
@@ -79,10 +81,26 @@ def worst_force_err(lat, case, hist):
     return worst
 
 
+def run_variant(case, storage, variant):
+    lat = B.Lattice.from_case(case, storage=storage, history_len=128)
+    if variant:
+        lat.tune(variant, 0)
+    lat.step(100)
+    return lat
+
+
+def same_bits(a, b):
+    """Velocity fields and every body's force series of two runs agree bit for bit."""
+    for kind in (B.FIELD_UX, B.FIELD_UY):
+        assert np.array_equal(a.field(kind), b.field(kind))
+    fa, fb = a.forces(-1, 0, 100), b.forces(-1, 0, 100)
+    assert np.array_equal(fa[0], fb[0]) and np.array_equal(fa[1], fb[1])
+
+
 def test_many_cylinders_8192x4096_100_steps(many_cylinders_oracle):
     case, sim, hist = many_cylinders_oracle
-    lat = B.Lattice.from_case(case, history_len=128)
-    lat.step(100)
+    lat = run_variant(case, B.BTDF_F32, 11)
+    same_bits(lat, run_variant(case, B.BTDF_F32, 0))
     e = vel_err(lat, sim)
     worst = worst_force_err(lat, case, hist)
     print(f"\n[8192x4096, 400 cylinders, 100 steps] velocity rel L2 {e:.2e}, "
@@ -94,8 +112,8 @@ def test_many_cylinders_8192x4096_100_steps(many_cylinders_oracle):
 @pytest.mark.parametrize("storage,name", [(B.BTDF_F16DEV, "f16"), (B.BTDF_BF16DEV, "bf16")])
 def test_many_cylinders_8192x4096_mixed_precision(many_cylinders_oracle, storage, name):
     case, sim, hist = many_cylinders_oracle
-    lat = B.Lattice.from_case(case, storage=storage, history_len=128)
-    lat.step(100)
+    lat = run_variant(case, storage, 12)
+    same_bits(lat, run_variant(case, storage, 0))
     e = vel_err(lat, sim)
     fx, fy = lat.forces(-1, 0, 100)
     ecd = ecl = 0.0
