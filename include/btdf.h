@@ -263,7 +263,9 @@ int btdf_profile_read(btdf_ctx *ctx, double *ms_ib, double *ms_lbm, int64_t *lau
 #define BTDF_VARIANT_COUNT 14
 
 /* Variant of the fused collide-stream kernel.  Results do not depend on it.
- *   0 automatic (2 for FP32 storage, 1 for FP16 / BF16)
+ *   0 automatic: on lattices of at least 2^23 nodes 11 for FP32 and 12 for
+ *     FP16 / BF16 storage, on smaller ones 2 for FP32 and 11 for FP16 / BF16
+ *     (the autotuner's usual picks on a GB300)
  *   1 register-pipelined warps, 4 nodes per lane (16-byte FP32 vectors)
  *   2 register-pipelined warps, 2 nodes per lane
  *   3 TMA-tiled CTAs: 128 x 8 node tiles, 2 pipeline stages

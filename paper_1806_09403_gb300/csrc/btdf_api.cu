@@ -326,6 +326,19 @@ bool is_tma(int v) {
     return v == kVarTma8x2 || v == kVarTma8x3 || v == kVarTma16x2 || v == kVarTmaWs8x2 || v == kVarTmaWs7x3;
 }
 
+// Variant 0 (automatic): the autotuner's usual picks on a GB300 with the L2
+// flushed per step.  From 2^23 nodes up the lattice streams from DRAM: the
+// prefetching 4-node kernel for FP32 (0.342 against 0.36-0.40 ms for variant
+// 2 on 8192 x 4096) and the warp-specialized TMA kernel for 16-bit storage
+// (0.220 against 0.260 ms).  Below, the step is latency-bound and the
+// register kernels with one row segment per warp win (variant 12 takes 25
+// against 20 us on 1600 x 800).
+int auto_variant(const btdf_ctx* ctx) {
+    const bool big = (long long)ctx->cfg.nx * ctx->cfg.ny >= (1LL << 23);
+    if (ctx->cfg.storage == kStoreF32) return big ? kVarReg4L2Pf : kVarReg2;
+    return big && ctx->tma_ok ? kVarTmaWs8x2 : kVarReg4L2Pf;
+}
+
 // Tensor map of a TMA variant: boxes of 10, 18 and 9 rows.
 int tmap_index(int v) { return v == kVarTma16x2 ? 1 : v == kVarTmaWs7x3 ? 2 : 0; }
 
@@ -439,7 +452,7 @@ int enqueue_step(btdf_ctx* ctx, cudaStream_t st, bool pull, int cur, bool prof) 
     // dependent of the IB kernel: its band nodes wait for the forces, the rest
     // of the lattice overlaps the IB stage.
     const bool pdl = ctx->nmark > 0 && !prof;
-    int v = ctx->variant == kVarAuto ? (ctx->cfg.storage == kStoreF32 ? kVarReg2 : kVarReg4) : ctx->variant;
+    int v = ctx->variant == kVarAuto ? auto_variant(ctx) : ctx->variant;
     if (is_tma(v) && (!pull || !ctx->tma_ok)) v = kVarReg4;   // TMA kernel pulls only
     // the box's first and last rows are rebuilt in the register kernels only
     if (ctx->d_box && (is_tma(v) || v == kVarReg4Pf || v == kVarReg2Pf)) v = kVarReg4;
