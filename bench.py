@@ -639,6 +639,9 @@ def our_arm(args):
                      "kernel_ms_per_launch": m["kernel_ms_per_launch"],
                      "ib_ms_per_step": m["ib_ms_per_step"],
                      "ib_ms_per_step_warm_l2": m["ib_ms_per_step_warm"], "ib_markers": nmark,
+                     # what the IB stage adds to the timed step (both L2-flushed):
+                     # median step time minus the collide-stream kernel's time
+                     "ib_exposed_ms_per_step": m["ms_per_step_median"] - m["kernel_ms_per_launch"],
                      "peak_source": peak_src},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e, "unit": "MLUPS", "h2d_bytes_per_step": 16 * nmark,
