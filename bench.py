@@ -411,6 +411,28 @@ def measure_storage(B, case, storage, args, stream, world, flush_l2, barrier, la
     if args.variant == 0:
         best, tms = lat.autotune(tune_steps, True)
         tune = {VARIANT_NAMES[v]: t for v, t in tms.items()}
+        # The library's tuner and this loop time a step the same way but can
+        # rank near-equal variants differently (on 1600 x 800 the tuner saw
+        # variants 1 and 2 within 0.3 us; this loop timed them 2 us apart).
+        # Re-time its three fastest here, as the timed region will, and keep
+        # the fastest.
+        recheck = {}
+        for v in sorted(tms, key=tms.get)[:3]:
+            lat.tune(v, 0)
+            lat.step(3)
+            pairs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                     for _ in range(16)]
+            for a, b in pairs:
+                flush_l2()
+                a.record(stream)
+                lat.step(1)
+                b.record(stream)
+            torch.cuda.synchronize()
+            recheck[v] = float(np.mean([a.elapsed_time(b) for a, b in pairs]))
+        best = min(recheck, key=recheck.get)
+        tune = {"library_tuner": tune,
+                "recheck_mean_ms": {VARIANT_NAMES[v]: t for v, t in recheck.items()}}
+        lat.tune(best, 0)
     else:
         best, tune = args.variant, {}
         lat.tune(best, 0)
@@ -640,8 +662,8 @@ def our_arm(args):
                      "ib_ms_per_step": m["ib_ms_per_step"],
                      "ib_ms_per_step_warm_l2": m["ib_ms_per_step_warm"], "ib_markers": nmark,
                      # what the IB stage adds to the timed step (both L2-flushed):
-                     # median step time minus the collide-stream kernel's time
-                     "ib_exposed_ms_per_step": m["ms_per_step_median"] - m["kernel_ms_per_launch"],
+                     # mean step time minus the collide-stream kernel's mean time
+                     "ib_exposed_ms_per_step": m["ms_per_step"] - m["kernel_ms_per_launch"],
                      "peak_source": peak_src},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e, "unit": "MLUPS", "h2d_bytes_per_step": 16 * nmark,
@@ -658,8 +680,9 @@ def our_arm(args):
                                        "flushed outside the timing before each step"}},
         "gpu_launches": int(args.steps * (m["n_ib"] + m["n_lbm"]) // max(m["n_lbm"], 1)),
         "kernel_variant": {"chosen": m["variant"], "ms_per_step_flushed": m["tune"],
-                           "tuner": "btdf_autotune: median of 32 steps per variant, L2 evicted "
-                                    "before each"},
+                           "tuner": "btdf_autotune: interquartile mean of 32 steps per variant, L2 evicted "
+                                    "before each; its three fastest re-timed over 16 steps in this "
+                                    "script's timed-loop conditions, the fastest kept"},
         "clocks": clk.summary(),
         "graph_warm_mlups": warm,
         "cd_err_vs_fp64": cd_err or None,

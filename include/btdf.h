@@ -311,10 +311,11 @@ int btdf_device_bytes(const btdf_ctx *ctx, size_t *bytes);
  * this context's own lattice, `steps` steps each after 3 untimed ones, every
  * step (IB and LBM stage, overlapped as in btdf_step) between CUDA events on
  * the context stream, with the L2 cache evicted before each step when
- * flush_l2 != 0.  Keeps the variant with the lowest median step time.  The
+ * flush_l2 != 0.  Keeps the variant with the lowest interquartile mean step
+ * time (the mean of the middle half of the sorted times).  The
  * populations, the step counter, the force history and the last step's
  * marker results are restored afterwards, so the simulation does not
- * advance.  Outputs (may be NULL): *chosen, and ms[v] = median ms per step of
+ * advance.  Outputs (may be NULL): *chosen, and ms[v] = that mean, in ms per step, of
  * variant v for v = 0..BTDF_VARIANT_COUNT-1 (-1 where not timed).  Needs temporary device memory
  * for one copy of the populations and, with flush_l2, four times the L2 size.
  * Synchronizes.  Errors: EINVAL (steps outside 1..100000), ESTATE (no fields),

@@ -356,7 +356,7 @@ class Lattice:
 
     def autotune(self, steps=20, flush_l2=True):
         """Times every collide-stream variant on this lattice (btdf_autotune),
-        keeps the fastest; returns (chosen, {variant: median ms per step})."""
+        keeps the fastest; returns (chosen, {variant: interquartile mean ms per step})."""
         ch = C.c_int32()
         ms = np.zeros(VARIANT_COUNT, dtype=np.float32)
         self._check(lib().btdf_autotune(self._ctx, int(steps), 1 if flush_l2 else 0, C.byref(ch),

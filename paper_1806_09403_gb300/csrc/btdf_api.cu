@@ -1590,8 +1590,7 @@ int btdf_autotune(btdf_ctx* ctx, int32_t steps, int32_t flush_l2, int32_t* chose
             CK(cudaStreamSynchronize(st));
             std::vector<float> t(steps);
             for (int i = 0; i < steps; i++) CK(cudaEventElapsedTime(&t[i], ev[2 * i], ev[2 * i + 1]));
-            std::sort(t.begin(), t.end());
-            res[v] = t[steps / 2];
+            res[v] = interquartile_mean(t);
             if (v == 1 || res[v] < best_ms) {
                 best_ms = res[v];
                 best = v;

@@ -635,8 +635,7 @@ int btdf_batch_autotune(btdf_batch* bt, int32_t steps, int32_t flush_l2, int32_t
             BCK(cudaStreamSynchronize(st));
             std::vector<float> t(steps);
             for (int i = 0; i < steps; i++) BCK(cudaEventElapsedTime(&t[i], ev[2 * i], ev[2 * i + 1]));
-            std::sort(t.begin(), t.end());
-            res[v] = t[steps / 2];
+            res[v] = interquartile_mean(t);
             if (v == 1 || res[v] < res[best]) best = v;
         }
         return BTDF_OK;

@@ -2,6 +2,7 @@
 // the BTDF-IB/LBM library (not part of the public C ABI).
 #pragma once
 
+#include <algorithm>
 #include <cstdint>
 #include <vector>
 #include <cuda.h>
@@ -236,6 +237,19 @@ cudaError_t launch_ib_force_batch(int storage, bool pull, int width, const void*
                                   const IbParams& q, cudaStream_t st);
 int tma_box_rows(int variant);
 int tma_halo(int storage);
+
+// Statistic of the autotuners: the mean of the middle half of the per-step
+// times (all of them below four).  CUDA event times come in steps of about a
+// microsecond on this hardware, so the median of a few dozen steps ties
+// variants that differ by less; the mean resolves below that step, and
+// dropping the outer quarters keeps it robust to outliers.
+inline float interquartile_mean(std::vector<float> t) {
+    std::sort(t.begin(), t.end());
+    const size_t n = t.size(), lo = n >= 4 ? n / 4 : 0, hi = n >= 4 ? n - n / 4 : n;
+    double s = 0.0;
+    for (size_t i = lo; i < hi; i++) s += t[i];
+    return hi > lo ? (float)(s / (double)(hi - lo)) : 0.0f;
+}
 // pdl: launch as a programmatic dependent of the preceding kernel (the IB
 // kernel loads its marker tables, then waits for that kernel's results).
 cudaError_t launch_ib_force(int storage, bool pull, int width, const void* g,
