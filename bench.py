@@ -692,6 +692,7 @@ def our_arm(args):
                                 "kernel_ms_per_launch": v["kernel_ms_per_launch"],
                                 "achieved_gbs": v["achieved_gbs"], "frac": v["frac"],
                                 "traffic": v["traffic"], "bytes_per_lu": 36,
+                                "ib_exposed_ms_per_step": v["ms_per_step"] - v["kernel_ms_per_launch"],
                                 "variant": v["variant"], "speedup_vs_f32": v["value"] / value}
                             for k, v in mixed.items()} or None,
         "batch": batch,
