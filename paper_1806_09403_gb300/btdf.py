@@ -346,8 +346,10 @@ class Lattice:
                                             C.byref(lb)), "btdf_profile_read")
         return a.value, b.value, la.value, lb.value
 
-    def tune(self, nodes_per_lane=0, grid_blocks=0):
-        self._check(lib().btdf_tune(self._ctx, int(nodes_per_lane), int(grid_blocks)), "btdf_tune")
+    def tune(self, variant=0, grid_blocks=0):
+        """Collide-stream kernel variant (btdf_tune: 0 automatic, 1 .. VARIANT_COUNT - 1)
+        and an optional cap on its grid (0: the variant's default)."""
+        self._check(lib().btdf_tune(self._ctx, int(variant), int(grid_blocks)), "btdf_tune")
 
     def device_bytes(self) -> int:
         n = C.c_size_t()
