@@ -264,8 +264,9 @@ int btdf_profile_read(btdf_ctx *ctx, double *ms_ib, double *ms_lbm, int64_t *lau
 
 /* Variant of the fused collide-stream kernel.  Results do not depend on it.
  *   0 automatic: on lattices of at least 2^23 nodes 11 for FP32 and 12 for
- *     FP16 / BF16 storage, on smaller ones 2 for FP32 and 11 for FP16 / BF16
- *     (the autotuner's usual picks on a GB300)
+ *     FP16 / BF16 storage (11 where no tensor maps could be encoded), on
+ *     smaller ones 2 for FP32 and 11 for FP16 / BF16 (the autotuner's usual
+ *     picks on a GB300)
  *   1 register-pipelined warps, 4 nodes per lane (16-byte FP32 vectors)
  *   2 register-pipelined warps, 2 nodes per lane
  *   3 TMA-tiled CTAs: 128 x 8 node tiles, 2 pipeline stages
@@ -289,6 +290,10 @@ int btdf_profile_read(btdf_ctx *ctx, double *ms_ib, double *ms_lbm, int64_t *lau
  * one 32 x NPL-node row segment per warp for variants 1, 2 and 8-11, so the
  * block scheduler balances the SMs; SM count x resident blocks per SM for
  * the persistent variants 3-7, 12 and 13.
+ * The TMA variants (3-5, 12, 13) run pulling steps only: the first step after
+ * btdf_init_fields (which streams in place) runs variant 1 instead, as do all
+ * steps of a lattice with the Taylor-Green box (BTDF_BCX_BOX), where variants
+ * 6 and 7 also give way to variant 1.
  * Synchronizes and drops cached CUDA graphs.
  * Errors: EINVAL (unknown variant, TMA variant without tensor maps). */
 int btdf_tune(btdf_ctx *ctx, int32_t variant, int32_t grid_blocks);
